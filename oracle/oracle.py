@@ -1,0 +1,156 @@
+"""CPU oracle for the X-engine: Python wrapper around ``corr_oracle.c`` plus the dump-format rules.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module. The product library never imports, links or calls it, and it
+shares no code with the CUDA path.
+
+Definitions it follows (paper: Sec. 1 O(N^2) cross multiplication, Sec. 2.5 GPU layer
+"cross multiplied and averaged", Table 1 note (a) polarisation products XX, YY, XY, YX,
+Sec. 2.6 auto-correlation cells, Sec. 2.2 4+4-bit requantised samples):
+
+* sample byte = (Re nibble << 4) | Im nibble, each nibble a 4-bit two's-complement integer;
+* ``cross[f, b(a, c), p * n_pol + q] = sum_t x_{a p}(t) conj(x_{c q}(t))`` for stations a >= c,
+  ``b(a, c) = a (a + 1) / 2 + c``, stored as int64 (re, im);
+* ``autos[f, m] = sum_t |x_m(t)|^2``.
+
+Dump formats (the paper stores visibilities as 32-bit floats after averaging, Sec. 2.5; the
+integer sum is the exact product, so two float views are defined on top of it):
+
+* CI64: the int64 sums themselves;
+* CF32: each int64 rounded to the nearest float32;
+* CF32_NORM: each int64 divided by the sample count in float64, then rounded to float32.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "corr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FMT_CI64, FMT_CF32, FMT_CF32_NORM = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc into ``oracle/_build/liboracle.so``; returns the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            p_u8 = ctypes.POINTER(ctypes.c_uint8)
+            p_i64 = ctypes.POINTER(ctypes.c_int64)
+            p_i32 = ctypes.POINTER(ctypes.c_int32)
+            lib.oracle_correlate.argtypes = [p_u8, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             p_i64, p_i64, ctypes.c_int]
+            lib.oracle_correlate.restype = ctypes.c_int
+            lib.oracle_cells.argtypes = [p_u8, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, p_i32, p_i64]
+            lib.oracle_cells.restype = ctypes.c_int
+            lib.oracle_autos.argtypes = [p_u8, ctypes.c_int, ctypes.c_int, ctypes.c_int, p_i64]
+            lib.oracle_autos.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check_samples(samples: np.ndarray) -> np.ndarray:
+    if samples.dtype != np.uint8 or samples.ndim != 3:
+        raise ValueError("samples must be a uint8 array of shape [T][C][N]")
+    return np.ascontiguousarray(samples)
+
+
+def n_baselines(n_inputs: int, n_pol: int) -> int:
+    s = n_inputs // n_pol
+    return s * (s + 1) // 2
+
+
+def correlate(samples: np.ndarray, n_pol: int, threads: int = 1):
+    """Full X-engine result for ``samples[T][C][N]``: ``(cross[C][B_s][n_pol^2][2], autos[C][N])``."""
+    samples = _check_samples(samples)
+    T, C, N = samples.shape
+    if n_pol not in (1, 2) or N % n_pol:
+        raise ValueError("bad n_pol")
+    bs = n_baselines(N, n_pol)
+    cross = np.zeros((C, bs, n_pol * n_pol, 2), dtype=np.int64)
+    autos = np.zeros((C, N), dtype=np.int64)
+    rc = _load().oracle_correlate(_ptr(samples, ctypes.c_uint8), N, C, T, n_pol, _ptr(cross, ctypes.c_int64),
+                                  _ptr(autos, ctypes.c_int64), int(threads))
+    if rc != 0:
+        raise RuntimeError("oracle_correlate failed: %d" % rc)
+    return cross, autos
+
+
+def cells(samples: np.ndarray, cell_list) -> np.ndarray:
+    """Visibility cells ``(f, i, j) -> sum_t x_{f,i}(t) conj(x_{f,j}(t))`` as int64 ``[k][2]``."""
+    samples = _check_samples(samples)
+    T, C, N = samples.shape
+    cl = np.ascontiguousarray(np.asarray(cell_list, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((cl.shape[0], 2), dtype=np.int64)
+    rc = _load().oracle_cells(_ptr(samples, ctypes.c_uint8), N, C, T, cl.shape[0], _ptr(cl, ctypes.c_int32),
+                              _ptr(out, ctypes.c_int64))
+    if rc != 0:
+        raise RuntimeError("oracle_cells failed: %d" % rc)
+    return out
+
+
+def autos(samples: np.ndarray) -> np.ndarray:
+    """Autocorrelations (total power) ``[C][N]`` int64."""
+    samples = _check_samples(samples)
+    T, C, N = samples.shape
+    out = np.zeros((C, N), dtype=np.int64)
+    rc = _load().oracle_autos(_ptr(samples, ctypes.c_uint8), N, C, T, _ptr(out, ctypes.c_int64))
+    if rc != 0:
+        raise RuntimeError("oracle_autos failed: %d" % rc)
+    return out
+
+
+def to_format(values: np.ndarray, fmt: int, n_samples: int) -> np.ndarray:
+    """Convert int64 sums to a dump format (CI64 / CF32 / CF32_NORM), element by element."""
+    values = np.asarray(values, dtype=np.int64)
+    if fmt == FMT_CI64:
+        return values.copy()
+    if fmt == FMT_CF32:
+        return values.astype(np.float32)
+    if fmt == FMT_CF32_NORM:
+        if n_samples <= 0:
+            return np.zeros(values.shape, dtype=np.float32)
+        return (values.astype(np.float64) / float(n_samples)).astype(np.float32)
+    raise ValueError("unknown format")
+
+
+def unpack(samples: np.ndarray):
+    """Packed bytes -> (re, im) int64 arrays of the same shape (sign-extended nibbles)."""
+    s = np.asarray(samples, dtype=np.uint8)
+    re = (s >> 4).astype(np.int64)
+    im = (s & 0xF).astype(np.int64)
+    re = np.where(re >= 8, re - 16, re)
+    im = np.where(im >= 8, im - 16, im)
+    return re, im
+
+
+def pack(re, im) -> np.ndarray:
+    """(re, im) integers in [-8, 7] -> packed bytes (Re in the high nibble)."""
+    re = np.asarray(re, dtype=np.int64)
+    im = np.asarray(im, dtype=np.int64)
+    if re.min(initial=0) < -8 or re.max(initial=0) > 7 or im.min(initial=0) < -8 or im.max(initial=0) > 7:
+        raise ValueError("components must lie in [-8, 7]")
+    return (((re & 0xF) << 4) | (im & 0xF)).astype(np.uint8)

@@ -1,0 +1,272 @@
+"""Pins for the CPU oracle: each test ties it to something other than itself.
+
+* brute force with numpy integer matrix products (exact) on tiny inputs, every cell;
+* closed forms: a rank-1 injected common signal (the exact version of the CW test tone of Sec. 5),
+  orthogonal Walsh-Hadamard codes (rank > 1), constant extremes, alternating signs;
+* an int64 overflow pin (a sum that wraps int32);
+* invariants: Hermitian auto-station blocks, real non-negative autos, Cauchy-Schwarz, linearity
+  in time, zero padding, permutation of inputs;
+* golden fixtures under tests/golden/ with hand-derived values.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rand_bytes(rng, T, C, N):
+    return rng.integers(0, 256, size=(T, C, N), dtype=np.uint8)
+
+
+def _brute_full(samples):
+    """Full N x N Hermitian matrix per channel via exact int64 matrix products."""
+    re, im = oracle.unpack(samples)  # [T][C][N]
+    out_re = np.einsum("tcn,tcm->cnm", re, re) + np.einsum("tcn,tcm->cnm", im, im)
+    out_im = np.einsum("tcn,tcm->cnm", im, re) - np.einsum("tcn,tcm->cnm", re, im)
+    return out_re, out_im
+
+
+def _triangle_from_full(full_re, full_im, n_pol):
+    C, N, _ = full_re.shape
+    S = N // n_pol
+    bs = S * (S + 1) // 2
+    out = np.zeros((C, bs, n_pol * n_pol, 2), dtype=np.int64)
+    for a in range(S):
+        for c in range(a + 1):
+            b = a * (a + 1) // 2 + c
+            for p in range(n_pol):
+                for q in range(n_pol):
+                    i, j = a * n_pol + p, c * n_pol + q
+                    out[:, b, p * n_pol + q, 0] = full_re[:, i, j]
+                    out[:, b, p * n_pol + q, 1] = full_im[:, i, j]
+    return out
+
+
+@pytest.mark.parametrize("n_pol", [1, 2])
+@pytest.mark.parametrize("shape", [(1, 1, 2), (7, 3, 4), (64, 2, 8), (33, 4, 6)])
+def test_brute_force_every_cell(n_pol, shape):
+    T, C, N = shape
+    rng = np.random.default_rng(1000 + T * 7 + N)
+    s = _rand_bytes(rng, T, C, N)
+    cross, autos = oracle.correlate(s, n_pol)
+    fr, fi = _brute_full(s)
+    np.testing.assert_array_equal(cross, _triangle_from_full(fr, fi, n_pol))
+    np.testing.assert_array_equal(autos, np.einsum("cnn->cn", fr))
+
+
+def test_threads_do_not_change_result():
+    rng = np.random.default_rng(5)
+    s = _rand_bytes(rng, 50, 9, 10)
+    a = oracle.correlate(s, 2, threads=1)
+    b = oracle.correlate(s, 2, threads=4)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_cells_match_brute_force_any_order():
+    rng = np.random.default_rng(6)
+    s = _rand_bytes(rng, 40, 3, 8)
+    fr, fi = _brute_full(s)
+    cl = [(f, i, j) for f in range(3) for i in range(8) for j in range(8)]
+    got = oracle.cells(s, cl)
+    for k, (f, i, j) in enumerate(cl):
+        assert got[k, 0] == fr[f, i, j] and got[k, 1] == fi[f, i, j]
+
+
+def test_autos_entry_point_matches_brute_force():
+    rng = np.random.default_rng(7)
+    s = _rand_bytes(rng, 30, 5, 12)
+    fr, _ = _brute_full(s)
+    np.testing.assert_array_equal(oracle.autos(s), np.einsum("cnn->cn", fr))
+
+
+def test_rank1_common_signal_closed_form():
+    """x_m(t) = c_m s(t), s(t) in {1, -1, i, -i}: V[m, n] = T c_m conj(c_n), A[m] = T |c_m|^2."""
+    rng = np.random.default_rng(11)
+    T, C, N, n_pol = 96, 2, 12, 2
+    cm = rng.integers(-7, 8, size=(C, N)) + 1j * rng.integers(-7, 8, size=(C, N))
+    st = np.array([1, -1, 1j, -1j])[rng.integers(0, 4, size=(T, C))]
+    x = st[:, :, None] * cm[None, :, :]
+    s = oracle.pack(np.real(x).astype(np.int64), np.imag(x).astype(np.int64))
+    cross, autos = oracle.correlate(s, n_pol)
+    S = N // n_pol
+    for f in range(C):
+        for a in range(S):
+            for c in range(a + 1):
+                b = a * (a + 1) // 2 + c
+                for p in range(n_pol):
+                    for q in range(n_pol):
+                        v = T * cm[f, a * n_pol + p] * np.conj(cm[f, c * n_pol + q])
+                        assert cross[f, b, p * n_pol + q, 0] == int(round(v.real))
+                        assert cross[f, b, p * n_pol + q, 1] == int(round(v.imag))
+        np.testing.assert_array_equal(autos[f], (T * np.abs(cm[f]) ** 2).round().astype(np.int64))
+
+
+def _hadamard(r):
+    h = np.array([[1]], dtype=np.int64)
+    for _ in range(r):
+        h = np.block([[h, h], [h, -h]])
+    return h
+
+
+def test_walsh_hadamard_codes_closed_form():
+    """x_m(t) = sum_k c_{mk} h_k(t) with orthogonal +-1 codes: V = T C C^H exactly (rank > 1)."""
+    rng = np.random.default_rng(12)
+    r, K, N, C = 6, 3, 10, 1
+    T = 2 ** r
+    h = _hadamard(r)[[3, 17, 40]]  # K codes, each length T
+    cre = rng.integers(-2, 3, size=(N, K))
+    cim = rng.integers(-2, 3, size=(N, K))
+    xre = (cre @ h).T  # [T][N]
+    xim = (cim @ h).T
+    s = oracle.pack(xre[:, None, :], xim[:, None, :])
+    cross, autos = oracle.correlate(s, 1)
+    cm = cre + 1j * cim
+    V = T * cm @ cm.conj().T
+    for a in range(N):
+        for c in range(a + 1):
+            b = a * (a + 1) // 2 + c
+            assert cross[0, b, 0, 0] == int(round(V[a, c].real))
+            assert cross[0, b, 0, 1] == int(round(V[a, c].imag))
+    np.testing.assert_array_equal(autos[0], np.round(np.real(np.diag(V))).astype(np.int64))
+    assert np.linalg.matrix_rank(V) == K
+
+
+@pytest.mark.parametrize("re,im,expect_re", [(-8, -8, 128), (7, 7, 98), (-8, 7, 113), (0, -8, 64)])
+def test_constant_extremes(re, im, expect_re):
+    T, C, N = 37, 2, 6
+    s = oracle.pack(np.full((T, C, N), re), np.full((T, C, N), im))
+    cross, autos = oracle.correlate(s, 2)
+    assert np.all(cross[..., 0] == expect_re * T)
+    assert np.all(cross[..., 1] == 0)
+    assert np.all(autos == expect_re * T)
+
+
+def test_alternating_signs_cancel():
+    """Input 0 alternates sign each sample, input 1 is constant: their product sums to 0 over even T."""
+    T = 64
+    re = np.zeros((T, 1, 2), dtype=np.int64)
+    im = np.zeros((T, 1, 2), dtype=np.int64)
+    sign = np.where(np.arange(T) % 2 == 0, 1, -1)
+    re[:, 0, 0] = 5 * sign
+    im[:, 0, 0] = -3 * sign
+    re[:, 0, 1] = 4
+    im[:, 0, 1] = 2
+    cross, autos = oracle.correlate(oracle.pack(re, im), 1)
+    assert tuple(cross[0, 1, 0]) == (0, 0)  # pair (1, 0)
+    assert autos[0, 0] == 34 * T and autos[0, 1] == 20 * T
+
+
+def test_int64_overflow_pin():
+    """2^25 samples of -8-8i: Re V = 128 * 2^25 = 2^32, which an int32 accumulator would wrap to 0."""
+    T = 2 ** 25
+    s = np.full((T, 1, 2), 0x88, dtype=np.uint8)
+    cross, autos = oracle.correlate(s, 1)
+    assert np.all(cross[0, :, 0, 0] == 2 ** 32)
+    assert np.all(cross[0, :, 0, 1] == 0)
+    assert np.all(autos == 2 ** 32)
+
+
+def test_invariants_random():
+    rng = np.random.default_rng(21)
+    T, C, N, n_pol = 200, 3, 16, 2
+    s = _rand_bytes(rng, T, C, N)
+    cross, autos = oracle.correlate(s, n_pol)
+    S = N // n_pol
+    assert np.all(autos >= 0)
+    for a in range(S):
+        b = a * (a + 1) // 2 + a
+        xx, xy, yx, yy = cross[:, b, 0], cross[:, b, 1], cross[:, b, 2], cross[:, b, 3]
+        # auto-station XX / YY are real and equal the autos; YX = conj(XY)
+        np.testing.assert_array_equal(xx[:, 0], autos[:, 2 * a])
+        np.testing.assert_array_equal(yy[:, 0], autos[:, 2 * a + 1])
+        assert np.all(xx[:, 1] == 0) and np.all(yy[:, 1] == 0)
+        np.testing.assert_array_equal(yx[:, 0], xy[:, 0])
+        np.testing.assert_array_equal(yx[:, 1], -xy[:, 1])
+    # Cauchy-Schwarz |V_mn|^2 <= A_m A_n
+    for a in range(S):
+        for c in range(a + 1):
+            b = a * (a + 1) // 2 + c
+            for p in range(2):
+                for q in range(2):
+                    v = cross[:, b, p * 2 + q]
+                    mag2 = v[:, 0] ** 2 + v[:, 1] ** 2
+                    assert np.all(mag2 <= autos[:, 2 * a + p] * autos[:, 2 * c + q])
+
+
+def test_linearity_and_zero_padding():
+    rng = np.random.default_rng(22)
+    s1 = _rand_bytes(rng, 57, 2, 8)
+    s2 = _rand_bytes(rng, 31, 2, 8)
+    c1, a1 = oracle.correlate(s1, 2)
+    c2, a2 = oracle.correlate(s2, 2)
+    c12, a12 = oracle.correlate(np.concatenate([s1, s2]), 2)
+    np.testing.assert_array_equal(c12, c1 + c2)
+    np.testing.assert_array_equal(a12, a1 + a2)
+    cz, az = oracle.correlate(np.concatenate([s1, np.zeros((40, 2, 8), np.uint8)]), 2)
+    np.testing.assert_array_equal(cz, c1)
+    np.testing.assert_array_equal(az, a1)
+
+
+def test_permutation_of_inputs():
+    """Swapping inputs 1 and 4 (n_pol = 1) moves V[4, 1] to conj(V[4, 1]) at the swapped position."""
+    rng = np.random.default_rng(23)
+    s = _rand_bytes(rng, 45, 1, 6)
+    c0, a0 = oracle.correlate(s, 1)
+    perm = np.array([0, 4, 2, 3, 1, 5])
+    cp, ap = oracle.correlate(s[:, :, perm], 1)
+    np.testing.assert_array_equal(ap[0], a0[0][perm])
+
+    def full(cr):
+        V = np.zeros((6, 6), dtype=np.complex128)
+        for a in range(6):
+            for c in range(a + 1):
+                v = cr[0, a * (a + 1) // 2 + c, 0]
+                V[a, c] = v[0] + 1j * v[1]
+                V[c, a] = v[0] - 1j * v[1]
+        return V
+
+    np.testing.assert_array_equal(full(cp), full(c0)[np.ix_(perm, perm)])
+
+
+def test_dump_formats():
+    v = np.array([0, 1, -3, 2 ** 31 + 1, 2 ** 40 + 3, -(2 ** 33) - 7], dtype=np.int64)
+    np.testing.assert_array_equal(oracle.to_format(v, oracle.FMT_CI64, 10), v)
+    f = oracle.to_format(v, oracle.FMT_CF32, 10)
+    assert f.dtype == np.float32
+    assert f[3] == np.float32(2 ** 31) and f[4] == np.float32(2 ** 40)
+    n = oracle.to_format(v, oracle.FMT_CF32_NORM, 3)
+    assert n[2] == np.float32(-1.0) and n[1] == np.float32(1 / 3)
+    assert np.all(oracle.to_format(v, oracle.FMT_CF32_NORM, 0) == 0)
+
+
+def test_golden_fixtures():
+    """Hand-derived values (see each fixture's "derivation" field)."""
+    files = sorted(f for f in os.listdir(GOLDEN) if f.startswith("xengine_") and f.endswith(".json"))
+    assert files, "no golden fixtures"
+    for name in files:
+        with open(os.path.join(GOLDEN, name)) as fh:
+            g = json.load(fh)
+        re = np.array(g["re"], dtype=np.int64)
+        im = np.array(g["im"], dtype=np.int64)
+        s = oracle.pack(re, im)
+        cross, autos = oracle.correlate(s, g["n_pol"])
+        np.testing.assert_array_equal(cross, np.array(g["cross"], dtype=np.int64), err_msg=name)
+        np.testing.assert_array_equal(autos, np.array(g["autos"], dtype=np.int64), err_msg=name)
+
+
+def test_pack_unpack_roundtrip_and_range():
+    vals = np.arange(-8, 8)
+    re, im = np.meshgrid(vals, vals)
+    b = oracle.pack(re, im)
+    r2, i2 = oracle.unpack(b)
+    np.testing.assert_array_equal(r2, re)
+    np.testing.assert_array_equal(i2, im)
+    assert oracle.pack(np.array([-8]), np.array([7]))[0] == 0x87
+    with pytest.raises(ValueError):
+        oracle.pack(np.array([8]), np.array([0]))

@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark of the X-engine hot path on the 512-input, 128-channel workload.
+
+One step = one pass of the whole hot path over one batch: 16 corr_accumulate calls of 8192-sample
+blocks (N = 512 inputs = 256 dual-pol stations, C = 128 channels, 4+4-bit Gaussian-plus-tone samples;
+unpack -> cross-multiply -> flush to int64, autos from the diagonal) followed by a dump of the cross
+and auto accumulators with reset (the integrate-and-dump step). Inputs (16 distinct blocks, 8 GiB)
+are resident in HBM before timing; they exceed L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0). Metric: useful Tera-CMAC/s = N (N + 1) / 2 * C * T / time / 1e12, plus
+the real-time factor at the 24.0 kHz channel rate. `--impl reference` times the CPU oracle instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--path fp8tc|fp32] [--impl reference]
+Multi-GPU: launched by torch.distributed.run; channels are independent, every rank runs the same
+per-GPU workload on its own GPU (weak scaling), no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Tera-CMAC/s + real-time factor, 512-input 4-bit X-engine: int8-TC vs FP32 path"
+N_IN, N_CHAN, T_BLOCK, N_BLOCKS, N_POL = 512, 128, 8192, 16, 2
+CHANNEL_RATE_HZ = 24000.0  # 98.304 MHz / 4096 (Sec. 2)
+SEED = 0x14113751 + 2
+WORKLOAD = "N=512 inputs (256 dual-pol stations), 128 channels, 16 blocks x 8192 samples per step, 4+4-bit Gaussian sigma=2.5 + common tone rho=0.1"
+
+
+def useful_cmacs(N, C, T):
+    return N * (N + 1) // 2 * C * T
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(seconds_target=15.0):
+    """Time the CPU oracle on a bounded sample of the workload (all host cores, channels in parallel)."""
+    import numpy as np
+
+    from oracle import oracle
+    from paper_1411_3751_gb300 import synth
+
+    cores = os.cpu_count() or 1
+    spec = synth.Spec(kind="gauss_tone", seed=SEED)
+    # calibration: one channel x 1024 samples on one thread
+    x = synth.generate_host(spec, 1024, 1, N_IN)
+    t0 = time.perf_counter()
+    oracle.correlate(x, N_POL, threads=1)
+    per_cmac = (time.perf_counter() - t0) / useful_cmacs(N_IN, 1, 1024)
+    chans = cores
+    T = int(seconds_target / (per_cmac * useful_cmacs(N_IN, 1, 1)) / 1.0) if per_cmac > 0 else 1024
+    T = max(256, min(T_BLOCK, (T // 256) * 256))
+    x = synth.generate_host(spec, T, chans, N_IN)
+    t0 = time.perf_counter()
+    oracle.correlate(x, N_POL, threads=cores)
+    dt = time.perf_counter() - t0
+    cm = useful_cmacs(N_IN, chans, T)
+    return {"value": cm / dt / 1e12, "unit": "Tera-CMAC/s", "cores": cores, "kind": "oracle",
+            "sample": "%d channels x %d samples x %d inputs (of 128 x 131072 x 512), %.1f s, threads across channels"
+                      % (chans, T, N_IN, dt),
+            "real_time_factor": (T / CHANNEL_RATE_HZ) / dt * (chans / N_CHAN)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import numpy as np
+
+    from oracle import oracle
+    from paper_1411_3751_gb300 import synth
+
+    cores = os.cpu_count() or 1
+    spec = synth.Spec(kind="gauss_tone", seed=SEED)
+    chans, T = cores, 512
+    x = synth.generate_host(spec, T, chans, N_IN)
+    for _ in range(max(0, args.warmup)):
+        oracle.correlate(x[:64], N_POL, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.correlate(x, N_POL, threads=cores)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    cm = useful_cmacs(N_IN, chans, T) * args.steps
+    value = cm / dt / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Tera-CMAC/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN,
+                                            "n_time_per_step": T_BLOCK * N_BLOCKS, "n_pol": N_POL},
+            "cpu_baseline": {"value": value, "unit": "Tera-CMAC/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: %d channels x %d samples x %d inputs on %d threads" % (chans, T, N_IN, cores)},
+            "e2e": {"value": value, "unit": "Tera-CMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp32"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import __graft_entry__
+
+    world, rank, local = dist_setup(args.gpus)
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1411_3751_gb300", "_build", "libcorr.so")):
+        __graft_entry__.build()
+    barrier(world)
+    from paper_1411_3751_gb300 import corr, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    spec = synth.Spec(kind="gauss_tone", seed=SEED + 1000 * rank)
+    blocks = [synth.generate_device(spec, T_BLOCK, N_CHAN, N_IN, t0=b * T_BLOCK) for b in range(N_BLOCKS)]
+    torch.cuda.synchronize()
+    xc = corr.Correlator(N_IN, N_CHAN, T_BLOCK, N_POL, path=args.path)
+    cross_out = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64, device=dev)
+    autos_out = torch.empty(xc.out_shape(corr.CORR_WHAT_AUTO), dtype=torch.int64, device=dev)
+
+    def step():
+        for b in range(N_BLOCKS):
+            xc.accumulate(blocks[b])
+        xc.dump(corr.CORR_WHAT_CROSS, reset=True, out=cross_out)
+        xc.dump(corr.CORR_WHAT_AUTO, reset=True, out=autos_out)
+
+    for _ in range(args.warmup):
+        step()
+    xc.sync()
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    xc.profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    xeng_ms, xeng_n = xc.profile_read(corr.CORR_KERNEL_XENG)
+    unpack_ms, unpack_n = xc.profile_read(corr.CORR_KERNEL_UNPACK)
+    dump_ms, dump_n = xc.profile_read(corr.CORR_KERNEL_DUMP)
+    xc.profile(False)
+    clk = clocks.stop()
+    xc.sync()
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    cm_step = useful_cmacs(N_IN, N_CHAN, T_BLOCK * N_BLOCKS)
+    value = cm_step * args.steps * world / (ms_total / 1e3) / 1e12
+    rtf = (T_BLOCK * N_BLOCKS / CHANNEL_RATE_HZ) / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (the X-engine), from its live event timings
+    peaks, peak_src = load_peaks()
+    per_launch_ms = xeng_ms / max(1, xeng_n)
+    flops_launch = 8.0 * useful_cmacs(N_IN, N_CHAN, T_BLOCK)
+    if args.path == "fp8tc":
+        peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        peak_note = "%s bf16 sustained x 2 (nominal fp8/bf16 ratio)" % peak_src
+        bound = "tensor"
+    else:
+        peak = 77.9  # FP32 FMA peak measured by a microbenchmark on this GPU at 1.95 GHz
+        peak_note = "FP32 FMA microbenchmark (152 SMs x 128 lanes x 2 flop)"
+        bound = "alu"
+    achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "f8_xeng_kernel" if args.path == "fp8tc" else "xeng_fp32_kernel",
+            "peak_source": peak_note, "launch_ms": per_launch_ms,
+            "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop" % flops_launch}
+
+    # end-to-end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_blocks = [blocks[b].cpu().pin_memory() for b in range(N_BLOCKS)]
+        cross_h = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64).pin_memory()
+        autos_h = torch.empty(xc.out_shape(corr.CORR_WHAT_AUTO), dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            for b in range(N_BLOCKS):
+                xc.accumulate_host(host_blocks[b])
+            xc.dump(corr.CORR_WHAT_CROSS, reset=True, out=cross_h)
+            xc.dump(corr.CORR_WHAT_AUTO, reset=True, out=autos_h)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e = {"value": cm_step * args.e2e_steps * world / (e_ms / 1e3) / 1e12, "unit": "Tera-CMAC/s",
+               "h2d_bytes_per_step": N_BLOCKS * T_BLOCK * N_CHAN * N_IN,
+               "d2h_bytes_per_step": cross_h.numel() * 8 + autos_h.numel() * 8,
+               "ms_per_step": e_ms / args.e2e_steps}
+        del host_blocks
+
+    # same-GPU FP32 path on the same workload (comparison leg of the metric)
+    fp32 = None
+    if args.path == "fp8tc" and args.fp32_steps > 0:
+        xc.set_path("fp32")
+        step()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp32_steps):
+            step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = max_over_ranks(f0.elapsed_time(f1), world) / args.fp32_steps
+        fp32 = {"value": cm_step * world / (f_ms / 1e3) / 1e12, "unit": "Tera-CMAC/s", "ms_per_step": f_ms,
+                "real_time_factor": (T_BLOCK * N_BLOCKS / CHANNEL_RATE_HZ) / (f_ms / 1e3)}
+        xc.set_path(args.path)
+    xc.sync()
+    xc.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        launches_per_step = N_BLOCKS * (2 if args.path == "fp8tc" else 1) + 2
+        line = {
+            "metric": METRIC, "value": value, "unit": "Tera-CMAC/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "e4m3" if args.path == "fp8tc" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN, "n_time_per_block": T_BLOCK,
+                       "blocks_per_step": N_BLOCKS, "n_pol": N_POL, "path": args.path,
+                       "l2": "inputs 8 GiB > L2, no flush needed", "parallelism": "channels per GPU (replicas)"},
+            "real_time_factor": rtf,
+            "roofline": roof,
+            "kernel_ms_per_step": {"xeng": xeng_ms / args.steps, "unpack": unpack_ms / args.steps,
+                                   "dump": dump_ms / args.steps},
+            "gpu_launches": (xeng_n + unpack_n + dump_n),
+            "gpu_launches_per_step": launches_per_step,
+            "clocks": clk,
+            "e2e": e2e,
+            "fp32_path": fp32,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

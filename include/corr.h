@@ -1,0 +1,176 @@
+/*
+ * corr.h - C ABI of libcorr, a single-GPU X-engine for a large-N FX radio correlator on GB300 (sm_103a).
+ *
+ * The library implements the O(N^2) stage of an FX correlator (paper Sec. 1: "O(N^2) cross
+ * multiplication" on GPUs; Sec. 2.5: spectra read in groups, "cross multiplied and averaged",
+ * 27 groups per 9 s dump). For every frequency channel f it accumulates
+ *
+ *     V_f = sum_t x_f(t) x_f(t)^H                 (N x N Hermitian, lower triangle stored)
+ *     A_f[m] = sum_t |x_{f,m}(t)|^2               (autocorrelations / total power, Sec. 2.6)
+ *
+ * over N inputs of 4+4-bit two's-complement complex samples (Sec. 2.2: requantisation to 4+4 bits).
+ * All arithmetic is exact: in-chip partial sums (FP32 registers, FP32 TMEM accumulators) are flushed
+ * into int64 device accumulators before they can lose a bit, so results equal the exact integer sums.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Samples  uint8 in[T][C][N] (time slowest, input fastest: channel-grouped data after the corner
+ *          turn of Sec. 2.3/2.4). Byte = (Re nibble << 4) | (Im nibble & 0xF), each nibble a 4-bit
+ *          two's-complement integer in [-8, 7]. Input index n = n_pol * station + pol, pol 0 = X, 1 = Y.
+ * Cross    [C][B_s][n_pol^2][2]: B_s = S (S + 1) / 2 station pairs (S = N / n_pol), pair index
+ *          b(a, c) = a (a + 1) / 2 + c for stations a >= c, product index p * n_pol + q in the order
+ *          XX, XY, YX, YY (Table 1 note (a) lists the four products), element
+ *          V[a p, c q] = sum_t x_{a p}(t) conj(x_{c q}(t)); last axis (re, im).
+ * Autos    [C][N]: sum_t |x_n(t)|^2 (real).
+ * Formats  CORR_FMT_CI64: int64 (re, im) / int64 autos, the exact sums.
+ *          CORR_FMT_CF32: float32, each int64 rounded to nearest.
+ *          CORR_FMT_CF32_NORM: float32 of (double)sum / (double)n_samples ("averaged", Sec. 2.5).
+ * Streams  every call that takes a `cuda_stream` (a cudaStream_t, NULL = legacy default stream)
+ *          only enqueues work on it and returns; work is ordered by the stream.
+ * Errors   functions return CORR_OK (0) or a negative corr_status; corr_last_error() gives a
+ *          thread-local message for the last failure on the calling thread. Nothing exits the process.
+ *          Device-side bounded waits that time out set a flag read by corr_sync().
+ * Memory   the library owns its device accumulators and scratch (allocated in corr_create, freed in
+ *          corr_destroy); callers own sample and output buffers. corr_footprint_bytes() states the
+ *          device bytes corr_create will allocate, for admission control.
+ * Threads  a context may be used by one host thread at a time.
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct corr_ctx corr_ctx;
+
+typedef enum corr_status {
+  CORR_OK = 0,
+  CORR_ERR_ARG = -1,     /* invalid argument (shape, pointer, enum value) */
+  CORR_ERR_CUDA = -2,    /* a CUDA runtime call failed (message in corr_last_error) */
+  CORR_ERR_OOM = -3,     /* device or host allocation failed */
+  CORR_ERR_STATE = -4,   /* call not valid in the context's current state */
+  CORR_ERR_TIMEOUT = -5, /* a device-side bounded wait gave up (reported by corr_sync) */
+  CORR_ERR_UNSUPPORTED = -6 /* path or mode not available on this device */
+} corr_status;
+
+typedef enum corr_path {
+  CORR_PATH_AUTO = 0,  /* fastest available: FP8 tensor path on sm_103a */
+  CORR_PATH_FP32 = 1,  /* FP32 FMA on CUDA cores (the arithmetic the paper's K20X X-engine used, Sec. 2.5) */
+  CORR_PATH_FP8TC = 3  /* tcgen05 kind::f8f6f4 e4m3 operands, FP32 accumulation in TMEM */
+} corr_path;
+
+typedef enum corr_what { CORR_WHAT_CROSS = 1, CORR_WHAT_AUTO = 2 } corr_what;
+
+typedef enum corr_fmt { CORR_FMT_CI64 = 0, CORR_FMT_CF32 = 1, CORR_FMT_CF32_NORM = 2 } corr_fmt;
+
+/* Kernel classes for corr_profile_read. */
+typedef enum corr_kernel {
+  CORR_KERNEL_XENG = 0,   /* cross-multiply-accumulate (FP32 or tensor-core X-engine) */
+  CORR_KERNEL_UNPACK = 1, /* 4+4-bit -> e4m3 operand build (tensor path) */
+  CORR_KERNEL_AUTOS = 2,  /* total-power kernel of corr_accumulate_autos */
+  CORR_KERNEL_DUMP = 3,   /* dump / format conversion */
+  CORR_KERNEL_COUNT = 4
+} corr_kernel;
+
+/*
+ * corr_create - make a context for n_inputs inputs (N), n_chans channels (C), blocks of
+ * n_time_per_block samples per channel (T), n_pol polarisations per station (1 or 2).
+ * Sec. 2.5: data are read in groups of 8000 spectra; T is that group size here.
+ * Allocates and zeroes the int64 accumulators and the path scratch on the current device.
+ * Returns NULL on error (corr_last_error). Rejects N < 1, C < 1, T < 1, n_pol not 1/2,
+ * N % n_pol != 0, sizes whose byte counts overflow, and footprints above free device memory (OOM).
+ */
+corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol);
+
+/* Select the arithmetic path (corr_path). Any time; accumulated sums are exact on every path. */
+int corr_set_path(corr_ctx* ctx, int path);
+
+/* Return the path that corr_accumulate will run (AUTO resolved). */
+int corr_get_path(const corr_ctx* ctx);
+
+/*
+ * corr_set_flush_period - maximum number of samples accumulated in on-chip FP32/int32 partial sums
+ * before they are added to the int64 accumulators (the paper integrates 8000-spectrum groups and
+ * then sums 27 of them, Sec. 2.5; the flush cadence is this library's choice). 0 restores the
+ * path default. Values are rounded down to the path's time granule; values above the path's
+ * exactness bound (FP32 and FP8 paths: 65536) are rejected with CORR_ERR_ARG.
+ */
+int corr_set_flush_period(corr_ctx* ctx, int n_samples);
+
+/*
+ * corr_accumulate - add one block of samples to the accumulators: V += sum_t x x^H and
+ * A += sum_t |x|^2 over the block's T samples, for all C channels.
+ * d_samples: device pointer to uint8[T][C][N] (caller-owned, must stay valid until the stream
+ * reaches the work). Asynchronous on cuda_stream. Returns CORR_ERR_ARG for a NULL pointer.
+ */
+int corr_accumulate(corr_ctx* ctx, const void* d_samples, void* cuda_stream);
+
+/*
+ * corr_accumulate_host - same as corr_accumulate for a HOST buffer uint8[T][C][N]: the library
+ * copies it to the device in time slices through its own staging buffers (overlapping copy and
+ * compute) and accumulates each slice. Pinned memory gives the best copy rate. Returns when the
+ * work is enqueued; the host buffer must stay valid until cuda_stream reaches the end of the work.
+ */
+int corr_accumulate_host(corr_ctx* ctx, const void* h_samples, void* cuda_stream);
+
+/*
+ * corr_accumulate_autos - add one block to the autocorrelations only (warp-shuffle reduction over
+ * time, no cross products): the high-cadence total-power path of Sec. 2.6, which the paper ran
+ * beside the main pipeline. Device pointer, same layout as corr_accumulate.
+ */
+int corr_accumulate_autos(corr_ctx* ctx, const void* d_samples, void* cuda_stream);
+
+/*
+ * corr_dump - write the accumulators selected by `what` (CORR_WHAT_CROSS or CORR_WHAT_AUTO) in
+ * format `fmt` to `out` (device pointer if is_device_ptr, else host pointer; host dumps go through
+ * a bounded device staging buffer and cudaMemcpyAsync, so pageable memory works and pinned memory
+ * is faster). Output sizes: cross C * B_s * n_pol^2 * 2 elements, autos C * N elements, of 8 bytes
+ * (CI64) or 4 bytes (CF32*). If reset != 0, the selected accumulators and their sample count are
+ * zeroed after the snapshot (Sec. 2.6: selective zeroing and dumping of accumulator cells, so the
+ * 1 s total-power cadence runs independently of the 9 s cross-power cadence).
+ */
+int corr_dump(corr_ctx* ctx, void* out, int is_device_ptr, int what, int fmt, int reset, void* cuda_stream);
+
+/* Samples per channel accumulated into `what` since creation or its last reset (host-side count). */
+long long corr_samples_accumulated(const corr_ctx* ctx, int what);
+
+/* Zero the selected accumulators (what = CROSS, AUTO or CROSS|AUTO) on cuda_stream. */
+int corr_reset(corr_ctx* ctx, int what, void* cuda_stream);
+
+/* Synchronize cuda_stream; return CORR_ERR_TIMEOUT if a device-side wait gave up (flag is cleared),
+ * CORR_ERR_CUDA on an asynchronous CUDA error, else CORR_OK. */
+int corr_sync(corr_ctx* ctx, void* cuda_stream);
+
+/* Device bytes corr_create(n_inputs, n_chans, n_time_per_block, n_pol) allocates for `path`
+ * (accumulators + path scratch + staging), or 0 for invalid arguments. */
+size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int n_pol, int path);
+
+/* Number of station pairs B_s = S (S + 1) / 2 for n_inputs / n_pol stations (0 if invalid). */
+long long corr_n_baselines(int n_inputs, int n_pol);
+
+/* Enable (on != 0) or disable per-kernel timing: when enabled, every kernel the context launches is
+ * bracketed by CUDA events recorded on the launching stream. Off by default. */
+int corr_profile_enable(corr_ctx* ctx, int on);
+
+/* Sum of recorded device durations (ms) and launch count for kernel class `kernel` (corr_kernel)
+ * since the last read; synchronizes on the recorded events, then clears the totals. */
+int corr_profile_read(corr_ctx* ctx, int kernel, double* total_ms, long long* launches);
+
+/* Synchronize the context's work, free its memory. NULL is accepted. */
+int corr_destroy(corr_ctx* ctx);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* corr_last_error(void);
+
+/* Library version string. */
+const char* corr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

@@ -1,0 +1,257 @@
+"""Python binding of libcorr's C ABI (include/corr.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes plain integers and
+pointers. :class:`Correlator` adds torch-tensor marshalling on top (data pointers, the current CUDA
+stream); all work runs in the library's CUDA kernels. There is no fallback: if the library cannot
+be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libcorr.so")
+
+CORR_OK = 0
+CORR_ERR_ARG, CORR_ERR_CUDA, CORR_ERR_OOM, CORR_ERR_STATE, CORR_ERR_TIMEOUT, CORR_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+CORR_PATH_AUTO, CORR_PATH_FP32, CORR_PATH_FP8TC = 0, 1, 3
+CORR_WHAT_CROSS, CORR_WHAT_AUTO = 1, 2
+CORR_FMT_CI64, CORR_FMT_CF32, CORR_FMT_CF32_NORM = 0, 1, 2
+CORR_KERNEL_XENG, CORR_KERNEL_UNPACK, CORR_KERNEL_AUTOS, CORR_KERNEL_DUMP = 0, 1, 2, 3
+
+PATHS = {"auto": CORR_PATH_AUTO, "fp32": CORR_PATH_FP32, "fp8tc": CORR_PATH_FP8TC}
+
+# (name, restype, argtypes) of every symbol include/corr.h declares
+_c_int, _c_ll, _c_sz, _c_vp, _c_cp = ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
+SIGNATURES = [
+    ("corr_create", _c_vp, [_c_int, _c_int, _c_int, _c_int]),
+    ("corr_set_path", _c_int, [_c_vp, _c_int]),
+    ("corr_get_path", _c_int, [_c_vp]),
+    ("corr_set_flush_period", _c_int, [_c_vp, _c_int]),
+    ("corr_accumulate", _c_int, [_c_vp, _c_vp, _c_vp]),
+    ("corr_accumulate_host", _c_int, [_c_vp, _c_vp, _c_vp]),
+    ("corr_accumulate_autos", _c_int, [_c_vp, _c_vp, _c_vp]),
+    ("corr_dump", _c_int, [_c_vp, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
+    ("corr_samples_accumulated", _c_ll, [_c_vp, _c_int]),
+    ("corr_reset", _c_int, [_c_vp, _c_int, _c_vp]),
+    ("corr_sync", _c_int, [_c_vp, _c_vp]),
+    ("corr_footprint_bytes", _c_sz, [_c_int, _c_int, _c_int, _c_int, _c_int]),
+    ("corr_n_baselines", _c_ll, [_c_int, _c_int]),
+    ("corr_profile_enable", _c_int, [_c_vp, _c_int]),
+    ("corr_profile_read", _c_int, [_c_vp, _c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    ("corr_destroy", _c_int, [_c_vp]),
+    ("corr_last_error", _c_cp, []),
+    ("corr_version", _c_cp, []),
+]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libcorr and attach the C signatures. Raises OSError if it is missing."""
+    if not os.path.exists(path):
+        raise OSError("libcorr is not built (%s missing): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load()
+
+
+class CorrError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = corr_last_error()
+        super().__init__("%s failed (%d): %s" % (where, code, msg))
+        self.code = code
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise CorrError(rc, where)
+    return rc
+
+
+# ---- C entry points, same names ---------------------------------------------------------------
+def corr_create(n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int) -> int:
+    h = _lib.corr_create(n_inputs, n_chans, n_time_per_block, n_pol)
+    if not h:
+        raise CorrError(CORR_ERR_ARG, "corr_create")
+    return h
+
+
+def corr_set_path(ctx: int, path: int) -> int:
+    return _check(_lib.corr_set_path(ctx, path), "corr_set_path")
+
+
+def corr_get_path(ctx: int) -> int:
+    return _check(_lib.corr_get_path(ctx), "corr_get_path")
+
+
+def corr_set_flush_period(ctx: int, n_samples: int) -> int:
+    return _check(_lib.corr_set_flush_period(ctx, n_samples), "corr_set_flush_period")
+
+
+def corr_accumulate(ctx: int, d_samples: int, stream: int) -> int:
+    return _check(_lib.corr_accumulate(ctx, d_samples, stream), "corr_accumulate")
+
+
+def corr_accumulate_host(ctx: int, h_samples: int, stream: int) -> int:
+    return _check(_lib.corr_accumulate_host(ctx, h_samples, stream), "corr_accumulate_host")
+
+
+def corr_accumulate_autos(ctx: int, d_samples: int, stream: int) -> int:
+    return _check(_lib.corr_accumulate_autos(ctx, d_samples, stream), "corr_accumulate_autos")
+
+
+def corr_dump(ctx: int, out: int, is_device_ptr: int, what: int, fmt: int, reset: int, stream: int) -> int:
+    return _check(_lib.corr_dump(ctx, out, is_device_ptr, what, fmt, reset, stream), "corr_dump")
+
+
+def corr_samples_accumulated(ctx: int, what: int) -> int:
+    return _check(_lib.corr_samples_accumulated(ctx, what), "corr_samples_accumulated")
+
+
+def corr_reset(ctx: int, what: int, stream: int) -> int:
+    return _check(_lib.corr_reset(ctx, what, stream), "corr_reset")
+
+
+def corr_sync(ctx: int, stream: int) -> int:
+    return _check(_lib.corr_sync(ctx, stream), "corr_sync")
+
+
+def corr_footprint_bytes(n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int, path: int) -> int:
+    return int(_lib.corr_footprint_bytes(n_inputs, n_chans, n_time_per_block, n_pol, path))
+
+
+def corr_n_baselines(n_inputs: int, n_pol: int) -> int:
+    return int(_lib.corr_n_baselines(n_inputs, n_pol))
+
+
+def corr_profile_enable(ctx: int, on: int) -> int:
+    return _check(_lib.corr_profile_enable(ctx, on), "corr_profile_enable")
+
+
+def corr_profile_read(ctx: int, kernel: int):
+    """Returns (total_ms, launches) recorded for `kernel` since the last read."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(_lib.corr_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)), "corr_profile_read")
+    return ms.value, n.value
+
+
+def corr_destroy(ctx: int) -> int:
+    return _check(_lib.corr_destroy(ctx), "corr_destroy")
+
+
+def corr_last_error() -> str:
+    return (_lib.corr_last_error() or b"").decode()
+
+
+def corr_version() -> str:
+    return (_lib.corr_version() or b"").decode()
+
+
+# ---- torch marshalling ---------------------------------------------------------------------
+def _stream_handle(stream) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Correlator:
+    """Owns one libcorr context; passes torch tensors' pointers and the current stream."""
+
+    def __init__(self, n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int = 2, path: str = "auto"):
+        self.n_inputs, self.n_chans, self.n_time, self.n_pol = n_inputs, n_chans, n_time_per_block, n_pol
+        self.n_baselines = corr_n_baselines(n_inputs, n_pol)
+        self.ctx = corr_create(n_inputs, n_chans, n_time_per_block, n_pol)
+        self.set_path(path)
+
+    def set_path(self, path: str):
+        corr_set_path(self.ctx, PATHS[path])
+
+    def set_flush_period(self, n: int):
+        corr_set_flush_period(self.ctx, n)
+
+    @property
+    def path(self) -> int:
+        return corr_get_path(self.ctx)
+
+    def _check_samples(self, x, device: bool):
+        import torch
+
+        if x.dtype != torch.uint8 or tuple(x.shape) != (self.n_time, self.n_chans, self.n_inputs):
+            raise ValueError("samples must be uint8 [T][C][N] = %s" % ((self.n_time, self.n_chans, self.n_inputs),))
+        if not x.is_contiguous():
+            raise ValueError("samples must be contiguous")
+        if x.is_cuda != device:
+            raise ValueError("samples must be on the %s" % ("device" if device else "host"))
+
+    def accumulate(self, samples, stream=None):
+        self._check_samples(samples, True)
+        corr_accumulate(self.ctx, samples.data_ptr(), _stream_handle(stream))
+
+    def accumulate_host(self, samples, stream=None):
+        self._check_samples(samples, False)
+        corr_accumulate_host(self.ctx, samples.data_ptr(), _stream_handle(stream))
+
+    def accumulate_autos(self, samples, stream=None):
+        self._check_samples(samples, True)
+        corr_accumulate_autos(self.ctx, samples.data_ptr(), _stream_handle(stream))
+
+    def out_shape(self, what: int):
+        if what == CORR_WHAT_CROSS:
+            return (self.n_chans, self.n_baselines, self.n_pol * self.n_pol, 2)
+        return (self.n_chans, self.n_inputs)
+
+    def dump(self, what: int = CORR_WHAT_CROSS, fmt: int = CORR_FMT_CI64, reset: bool = False, out=None,
+             device: bool = True, stream=None):
+        """Snapshot the accumulators into a new (or given) tensor on the device or the host."""
+        import torch
+
+        dtype = torch.int64 if fmt == CORR_FMT_CI64 else torch.float32
+        shape = self.out_shape(what)
+        if out is None:
+            out = torch.empty(shape, dtype=dtype, device="cuda" if device else "cpu",
+                              pin_memory=(not device))
+        if out.dtype != dtype or tuple(out.shape) != shape or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        corr_dump(self.ctx, out.data_ptr(), 1 if out.is_cuda else 0, what, fmt, 1 if reset else 0,
+                  _stream_handle(stream))
+        return out
+
+    def reset(self, what: int = CORR_WHAT_CROSS | CORR_WHAT_AUTO, stream=None):
+        corr_reset(self.ctx, what, _stream_handle(stream))
+
+    def samples(self, what: int = CORR_WHAT_CROSS) -> int:
+        return corr_samples_accumulated(self.ctx, what)
+
+    def sync(self, stream=None):
+        corr_sync(self.ctx, _stream_handle(stream))
+
+    def profile(self, on: bool = True):
+        corr_profile_enable(self.ctx, 1 if on else 0)
+
+    def profile_read(self, kernel: int):
+        return corr_profile_read(self.ctx, kernel)
+
+    def close(self):
+        if self.ctx:
+            corr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

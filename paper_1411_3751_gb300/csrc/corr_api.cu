@@ -1,0 +1,481 @@
+// C ABI of libcorr: argument validation, context and memory ownership, path dispatch, dumps.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "corr_internal.cuh"
+
+using namespace corr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(CORR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t kStageBytes = 64ull << 20;  // host-transfer staging buffer, x2
+
+struct Layout {
+  Shape s;
+  long long cross_elems;  // int64 elements
+  long long autos_elems;
+  int R;                  // FP8 operand rows
+  int T_pad;              // FP8 operand samples per channel
+  size_t op_bytes;
+  bool ok;
+};
+
+bool mul_ok(unsigned long long a, unsigned long long b, unsigned long long* out) {
+  if (a != 0 && b > ~0ull / a) return false;
+  *out = a * b;
+  return true;
+}
+
+Layout make_layout(int N, int C, int T, int npol) {
+  Layout L{};
+  L.ok = false;
+  if (N < 1 || C < 1 || T < 1 || (npol != 1 && npol != 2) || N % npol != 0) return L;
+  if (N > (1 << 20)) return L;
+  L.s.N = N;
+  L.s.C = C;
+  L.s.T = T;
+  L.s.npol = npol;
+  L.s.S = N / npol;
+  L.s.Bs = (long long)L.s.S * (L.s.S + 1) / 2;
+  L.s.P = npol * npol;
+  unsigned long long x;
+  if (!mul_ok((unsigned long long)C, (unsigned long long)L.s.Bs * L.s.P * 2, &x) || x > (1ull << 58)) return L;
+  L.cross_elems = (long long)x;
+  L.autos_elems = (long long)C * N;
+  L.R = (int)round_up(2LL * N, kF8RowAlign);
+  L.T_pad = (int)round_up(T, kF8Kt);
+  unsigned long long ob;
+  if (!mul_ok((unsigned long long)C * (unsigned long long)L.T_pad, (unsigned long long)L.R, &ob) || ob > (1ull << 46))
+    return L;
+  L.op_bytes = ob;
+  L.ok = true;
+  return L;
+}
+
+size_t footprint(const Layout& L, int path) {
+  size_t b = (size_t)(L.cross_elems + L.autos_elems) * 8 + 256;
+  b += 2 * kStageBytes;
+  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += L.op_bytes;
+  const long long nb = (L.s.N + 63) / 64;
+  b += (size_t)(nb * (nb + 1) / 2) * sizeof(int2) + (size_t)(nb * 8 + 8) * sizeof(F8Tile);
+  return b;
+}
+
+std::vector<int2> fp32_tiles(int N) {
+  std::vector<int2> t;
+  const int nb = (N + 63) / 64;
+  for (int ib = 0; ib < nb; ++ib)
+    for (int jb = 0; jb <= ib; ++jb) t.push_back(make_int2(ib, jb));
+  return t;
+}
+
+// FP8 tiles: c-side blocks of 64 inputs; a-side spans of 128 inputs (256 rows) starting at the
+// c-block, the first one halved for odd c-blocks (its lower half would hold only a < c).
+std::vector<F8Tile> fp8_tiles(int N, int R) {
+  std::vector<F8Tile> t;
+  const int ncb = (N + 63) / 64;
+  for (int cb = 0; cb < ncb; ++cb) {
+    int a0 = 64 * cb;
+    int nb = (cb & 1) ? 128 : 256;
+    while (a0 < N) {
+      if (2 * a0 + nb > R) nb = R - 2 * a0;
+      F8Tile x;
+      x.c0 = 64 * cb;
+      x.a0 = a0;
+      x.nb = nb;
+      x.pad = 0;
+      t.push_back(x);
+      a0 += nb / 2;
+      nb = 256;
+    }
+  }
+  return t;
+}
+
+}  // namespace
+
+// Opt-in per-kernel timing: CUDA events recorded on the launching stream around each launch.
+struct KernelTimer {
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+  size_t used = 0;
+  long long launches = 0;
+  double ms = 0.0;
+};
+
+struct corr_ctx {
+  Layout L;
+  bool profiling;
+  KernelTimer timers[CORR_KERNEL_COUNT];
+  int path;
+  int flush_len;  // 0 = path default
+  int device;
+  int num_sms;
+  long long* d_cross;
+  long long* d_autos;
+  int* d_err;
+  uint8_t* d_op;
+  CUtensorMap tmap;
+  int2* d_tiles32;
+  int n_tiles32;
+  F8Tile* d_tiles8;
+  int n_tiles8;
+  void* d_stage[2];
+  long long n_cross;
+  long long n_auto;
+};
+
+namespace {
+
+int resolved_path(const corr_ctx* c) { return c->path == CORR_PATH_AUTO ? CORR_PATH_FP8TC : c->path; }
+
+int flush_for(const corr_ctx* c, int path) {
+  if (c->flush_len > 0) {
+    const int g = path == CORR_PATH_FP32 ? kF32Kt : kF8Kt;
+    return (c->flush_len / g) * g;
+  }
+  return path == CORR_PATH_FP32 ? kDefaultFlushF32 : kDefaultFlushF8;
+}
+
+// Sum and recycle recorded event pairs (synchronizes on the last recorded stop event).
+void drain_timer(KernelTimer& t) {
+  for (size_t k = 0; k < t.used; ++k) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(t.ev[2 * k + 1]) == cudaSuccess && cudaEventElapsedTime(&ms, t.ev[2 * k], t.ev[2 * k + 1]) == cudaSuccess)
+      t.ms += ms;
+  }
+  t.used = 0;
+}
+
+bool timer_begin(corr_ctx* c, int k, cudaStream_t st) {
+  if (!c->profiling) return false;
+  KernelTimer& t = c->timers[k];
+  if (t.used >= 4096) drain_timer(t);
+  while (t.ev.size() < 2 * (t.used + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    t.ev.push_back(e);
+  }
+  cudaEventRecord(t.ev[2 * t.used], st);
+  return true;
+}
+
+void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun) {
+  if (!begun) return;
+  KernelTimer& t = c->timers[k];
+  cudaEventRecord(t.ev[2 * t.used + 1], st);
+  ++t.used;
+  ++t.launches;
+}
+
+void free_ctx(corr_ctx* c) {
+  if (!c) return;
+  for (int k = 0; k < CORR_KERNEL_COUNT; ++k)
+    for (cudaEvent_t e : c->timers[k].ev) cudaEventDestroy(e);
+  cudaFree(c->d_cross);
+  cudaFree(c->d_autos);
+  cudaFree(c->d_err);
+  cudaFree(c->d_op);
+  cudaFree(c->d_tiles32);
+  cudaFree(c->d_tiles8);
+  cudaFree(c->d_stage[0]);
+  cudaFree(c->d_stage[1]);
+  delete c;
+}
+
+// Accumulate T_blk samples from a device buffer laid out [T_blk][C][N].
+int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t st) {
+  const int path = resolved_path(c);
+  const int flush = flush_for(c, path);
+  cudaError_t e;
+  if (path == CORR_PATH_FP32) {
+    const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
+    e = launch_fp32(c->L.s, d_in, T_blk, flush, c->d_tiles32, c->n_tiles32, c->d_cross, c->d_autos, st);
+    timer_end(c, CORR_KERNEL_XENG, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "fp32 x-engine launch");
+  } else {
+    const int T_run = (int)round_up(T_blk, kF8Kt);
+    bool tb = timer_begin(c, CORR_KERNEL_UNPACK, st);
+    e = launch_f8_unpack(c->L.s, d_in, T_blk, T_run, c->L.T_pad, c->L.R, c->d_op, st);
+    timer_end(c, CORR_KERNEL_UNPACK, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "fp8 unpack launch");
+    tb = timer_begin(c, CORR_KERNEL_XENG, st);
+    e = launch_f8_xeng(c->L.s, &c->tmap, T_run, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
+                       c->num_sms, st);
+    timer_end(c, CORR_KERNEL_XENG, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "fp8 x-engine launch");
+  }
+  return CORR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* corr_last_error(void) { return g_err.c_str(); }
+
+const char* corr_version(void) { return "libcorr 0.1 (sm_103a)"; }
+
+long long corr_n_baselines(int n_inputs, int n_pol) {
+  if (n_inputs < 1 || (n_pol != 1 && n_pol != 2) || n_inputs % n_pol) return 0;
+  const long long s = n_inputs / n_pol;
+  return s * (s + 1) / 2;
+}
+
+size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int n_pol, int path) {
+  const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
+  if (!L.ok || (path != CORR_PATH_AUTO && path != CORR_PATH_FP32 && path != CORR_PATH_FP8TC)) return 0;
+  return footprint(L, path);
+}
+
+corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol) {
+  const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
+  if (!L.ok) {
+    fail(CORR_ERR_ARG, "corr_create: invalid shape (need N >= 1, C >= 1, T >= 1, n_pol in {1,2}, N % n_pol == 0, "
+                       "sizes within range)");
+    return nullptr;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "corr_create: cudaGetDevice");
+    return nullptr;
+  }
+  size_t free_b = 0, total_b = 0;
+  e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "corr_create: cudaMemGetInfo");
+    return nullptr;
+  }
+  if (footprint(L, CORR_PATH_AUTO) > free_b) {
+    fail(CORR_ERR_OOM, "corr_create: footprint " + std::to_string(footprint(L, CORR_PATH_AUTO)) +
+                           " bytes exceeds free device memory " + std::to_string(free_b));
+    return nullptr;
+  }
+  corr_ctx* c = new (std::nothrow) corr_ctx{};
+  if (!c) {
+    fail(CORR_ERR_OOM, "corr_create: host allocation");
+    return nullptr;
+  }
+  c->L = L;
+  c->path = CORR_PATH_AUTO;
+  c->device = dev;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (c->num_sms < 1) c->num_sms = 1;
+
+  const std::vector<int2> t32 = fp32_tiles(L.s.N);
+  const std::vector<F8Tile> t8 = fp8_tiles(L.s.N, L.R);
+  c->n_tiles32 = (int)t32.size();
+  c->n_tiles8 = (int)t8.size();
+  bool ok = cudaMalloc(&c->d_cross, (size_t)L.cross_elems * 8) == cudaSuccess &&
+            cudaMalloc(&c->d_autos, (size_t)L.autos_elems * 8) == cudaSuccess &&
+            cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_op, L.op_bytes) == cudaSuccess &&
+            cudaMalloc(&c->d_tiles32, t32.size() * sizeof(int2)) == cudaSuccess &&
+            cudaMalloc(&c->d_tiles8, t8.size() * sizeof(F8Tile)) == cudaSuccess &&
+            cudaMalloc(&c->d_stage[0], kStageBytes) == cudaSuccess &&
+            cudaMalloc(&c->d_stage[1], kStageBytes) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_ctx(c);
+    fail(CORR_ERR_OOM, "corr_create: device allocation failed");
+    return nullptr;
+  }
+  ok = cudaMemset(c->d_cross, 0, (size_t)L.cross_elems * 8) == cudaSuccess &&
+       cudaMemset(c->d_autos, 0, (size_t)L.autos_elems * 8) == cudaSuccess &&
+       cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess && cudaMemset(c->d_op, 0, L.op_bytes) == cudaSuccess &&
+       cudaMemcpy(c->d_tiles32, t32.data(), t32.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_tiles8, t8.data(), t8.size() * sizeof(F8Tile), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    e = cudaGetLastError();
+    free_ctx(c);
+    cuda_fail(e, "corr_create: initialisation");
+    return nullptr;
+  }
+  std::string err;
+  if (encode_op_tensor_map(&c->tmap, c->d_op, L.R, L.T_pad, L.s.C, &err) != 0) {
+    free_ctx(c);
+    fail(CORR_ERR_CUDA, "corr_create: " + err);
+    return nullptr;
+  }
+  return c;
+}
+
+int corr_set_path(corr_ctx* c, int path) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_set_path: NULL context");
+  if (path != CORR_PATH_AUTO && path != CORR_PATH_FP32 && path != CORR_PATH_FP8TC)
+    return fail(CORR_ERR_ARG, "corr_set_path: unknown path " + std::to_string(path));
+  c->path = path;
+  return CORR_OK;
+}
+
+int corr_get_path(const corr_ctx* c) { return c ? resolved_path(c) : CORR_ERR_ARG; }
+
+int corr_set_flush_period(corr_ctx* c, int n) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_set_flush_period: NULL context");
+  if (n < 0 || n > kF8MaxFlush) return fail(CORR_ERR_ARG, "corr_set_flush_period: must be in [0, 65536]");
+  const int g = resolved_path(c) == CORR_PATH_FP32 ? kF32Kt : kF8Kt;
+  if (n > 0 && n < g)
+    return fail(CORR_ERR_ARG, "corr_set_flush_period: below the path granule " + std::to_string(g));
+  c->flush_len = n;
+  return CORR_OK;
+}
+
+int corr_accumulate(corr_ctx* c, const void* d_samples, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_accumulate: NULL context");
+  if (!d_samples) return fail(CORR_ERR_ARG, "corr_accumulate: NULL samples");
+  const int rc = accumulate_device(c, static_cast<const uint8_t*>(d_samples), c->L.s.T, (cudaStream_t)stream);
+  if (rc != CORR_OK) return rc;
+  c->n_cross += c->L.s.T;
+  c->n_auto += c->L.s.T;
+  return CORR_OK;
+}
+
+int corr_accumulate_host(corr_ctx* c, const void* h_samples, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_accumulate_host: NULL context");
+  if (!h_samples) return fail(CORR_ERR_ARG, "corr_accumulate_host: NULL samples");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t row = (size_t)c->L.s.C * c->L.s.N;  // bytes per time sample
+  long long slice = (long long)(kStageBytes / row);
+  if (slice >= kF8Kt) slice = slice / kF8Kt * kF8Kt;
+  if (slice < 1) return fail(CORR_ERR_ARG, "corr_accumulate_host: one time sample exceeds the staging buffer");
+  const uint8_t* src = static_cast<const uint8_t*>(h_samples);
+  int buf = 0;
+  for (long long t0 = 0; t0 < c->L.s.T; t0 += slice) {
+    const int n = (int)((c->L.s.T - t0) < slice ? (c->L.s.T - t0) : slice);
+    cudaError_t e = cudaMemcpyAsync(c->d_stage[buf], src + (size_t)t0 * row, (size_t)n * row, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_accumulate_host: copy");
+    const int rc = accumulate_device(c, static_cast<const uint8_t*>(c->d_stage[buf]), n, st);
+    if (rc != CORR_OK) return rc;
+    buf ^= 1;
+  }
+  c->n_cross += c->L.s.T;
+  c->n_auto += c->L.s.T;
+  return CORR_OK;
+}
+
+int corr_accumulate_autos(corr_ctx* c, const void* d_samples, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_accumulate_autos: NULL context");
+  if (!d_samples) return fail(CORR_ERR_ARG, "corr_accumulate_autos: NULL samples");
+  const bool tb = timer_begin(c, CORR_KERNEL_AUTOS, (cudaStream_t)stream);
+  cudaError_t e = launch_autos(c->L.s, static_cast<const uint8_t*>(d_samples), c->L.s.T, c->d_autos, (cudaStream_t)stream);
+  timer_end(c, CORR_KERNEL_AUTOS, (cudaStream_t)stream, tb);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_accumulate_autos: launch");
+  c->n_auto += c->L.s.T;
+  return CORR_OK;
+}
+
+int corr_reset(corr_ctx* c, int what, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_reset: NULL context");
+  if (what < 1 || what > 3) return fail(CORR_ERR_ARG, "corr_reset: what must be CROSS, AUTO or both");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (what & CORR_WHAT_CROSS) {
+    cudaError_t e = cudaMemsetAsync(c->d_cross, 0, (size_t)c->L.cross_elems * 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_reset");
+    c->n_cross = 0;
+  }
+  if (what & CORR_WHAT_AUTO) {
+    cudaError_t e = cudaMemsetAsync(c->d_autos, 0, (size_t)c->L.autos_elems * 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_reset");
+    c->n_auto = 0;
+  }
+  return CORR_OK;
+}
+
+int corr_dump(corr_ctx* c, void* out, int is_device_ptr, int what, int fmt, int reset, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_dump: NULL context");
+  if (!out) return fail(CORR_ERR_ARG, "corr_dump: NULL output");
+  if (what != CORR_WHAT_CROSS && what != CORR_WHAT_AUTO) return fail(CORR_ERR_ARG, "corr_dump: what must be CROSS or AUTO");
+  if (fmt != CORR_FMT_CI64 && fmt != CORR_FMT_CF32 && fmt != CORR_FMT_CF32_NORM)
+    return fail(CORR_ERR_ARG, "corr_dump: unknown format");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long* acc = what == CORR_WHAT_CROSS ? c->d_cross : c->d_autos;
+  const long long n = what == CORR_WHAT_CROSS ? c->L.cross_elems : c->L.autos_elems;
+  const long long ns = what == CORR_WHAT_CROSS ? c->n_cross : c->n_auto;
+  const size_t esz = fmt == CORR_FMT_CI64 ? 8 : 4;
+  cudaError_t e;
+  if (is_device_ptr) {
+    const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
+    e = launch_dump(acc, n, out, fmt, ns, st);
+    timer_end(c, CORR_KERNEL_DUMP, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_dump: launch");
+  } else {
+    const long long per = (long long)(kStageBytes / esz);
+    int buf = 0;
+    for (long long k = 0; k < n; k += per) {
+      const long long m = (n - k) < per ? (n - k) : per;
+      const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
+      e = launch_dump(acc + k, m, c->d_stage[buf], fmt, ns, st);
+      timer_end(c, CORR_KERNEL_DUMP, st, tb);
+      if (e != cudaSuccess) return cuda_fail(e, "corr_dump: launch");
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + (size_t)k * esz, c->d_stage[buf], (size_t)m * esz,
+                          cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return cuda_fail(e, "corr_dump: copy");
+      buf ^= 1;
+    }
+  }
+  if (reset) return corr_reset(c, what, stream);
+  return CORR_OK;
+}
+
+long long corr_samples_accumulated(const corr_ctx* c, int what) {
+  if (!c) return CORR_ERR_ARG;
+  if (what == CORR_WHAT_CROSS) return c->n_cross;
+  if (what == CORR_WHAT_AUTO) return c->n_auto;
+  return CORR_ERR_ARG;
+}
+
+int corr_sync(corr_ctx* c, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_sync: NULL context");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_sync");
+  int flag = 0;
+  e = cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_sync: read error flag");
+  if (flag != 0) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return fail(CORR_ERR_TIMEOUT, "corr_sync: a device-side wait timed out (code " + std::to_string(flag) + ")");
+  }
+  return CORR_OK;
+}
+
+int corr_profile_enable(corr_ctx* c, int on) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_profile_enable: NULL context");
+  c->profiling = on != 0;
+  return CORR_OK;
+}
+
+int corr_profile_read(corr_ctx* c, int kernel, double* total_ms, long long* launches) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_profile_read: NULL context");
+  if (kernel < 0 || kernel >= CORR_KERNEL_COUNT) return fail(CORR_ERR_ARG, "corr_profile_read: unknown kernel id");
+  KernelTimer& t = c->timers[kernel];
+  drain_timer(t);
+  if (total_ms) *total_ms = t.ms;
+  if (launches) *launches = t.launches;
+  t.ms = 0.0;
+  t.launches = 0;
+  return CORR_OK;
+}
+
+int corr_destroy(corr_ctx* c) {
+  if (!c) return CORR_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_ctx(c);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_destroy: synchronize");
+  return CORR_OK;
+}
+
+}  // extern "C"

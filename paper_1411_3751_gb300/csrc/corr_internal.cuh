@@ -1,0 +1,76 @@
+// Internal declarations shared by the libcorr translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "corr.h"
+
+namespace corr {
+
+// ---------------------------------------------------------------------------------------------
+// Sizes and layouts
+// ---------------------------------------------------------------------------------------------
+// Accumulators (int64, owned by the context):
+//   cross[C][B_s][P][2]   exactly the public cross layout (corr.h), P = n_pol^2
+//   autos[C][N]
+// FP8 tensor path scratch (e4m3 operand, rebuilt by every corr_accumulate):
+//   op[C][T_pad][R]       R = round_up(2N, 128) operand rows per channel (row 2n = Re x_n,
+//                         row 2n + 1 = Im x_n, zero beyond 2N), T_pad = round_up(T, 128) time
+//                         columns (zero beyond T). Time is the contraction (K) dimension and the
+//                         rows are contiguous, i.e. an MN-major operand for the tensor cores.
+
+struct Shape {
+  int N, C, T, npol;
+  int S;        // stations
+  long long Bs; // station pairs
+  int P;        // products per pair
+};
+
+// FP8 path tile: c-side block of 64 inputs (128 operand rows, the MMA's M), a-side block starting
+// at input a0 with nb operand rows (128 or 256, the MMA's N).
+struct F8Tile {
+  int c0;
+  int a0;
+  int nb;
+  int pad;
+};
+
+constexpr int kF8Kt = 128;             // time samples per pipeline stage
+constexpr int kF8Stages = 4;           // smem ring depth
+constexpr int kF8RowAlign = 128;       // operand row padding
+constexpr int kF8MaxFlush = 65536;     // FP32 TMEM partials stay exact below 2^24 = 64 * 2^18
+constexpr int kF32Kt = 32;             // FP32 path time granule
+constexpr int kF32MaxFlush = 65536;    // |partial| <= 128 * 65536 = 2^23 < 2^24
+constexpr int kDefaultFlushF8 = 65536;
+constexpr int kDefaultFlushF32 = 65536;
+
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (each returns cudaSuccess or the launch error)
+// ---------------------------------------------------------------------------------------------
+cudaError_t launch_fp32(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const int2* d_tiles,
+                        int n_tiles, long long* d_cross, long long* d_autos, cudaStream_t st);
+
+cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long long* d_autos, cudaStream_t st);
+
+// T_blk valid samples; T_run = round_up(T_blk, kF8Kt) samples written; T_stride = op samples per channel.
+cudaError_t launch_f8_unpack(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
+                             uint8_t* d_op, cudaStream_t st);
+
+cudaError_t launch_f8_xeng(const Shape& s, const CUtensorMap* tmap, int T_run, int flush_len, const F8Tile* d_tiles,
+                           int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
+                           cudaStream_t st);
+
+size_t f8_smem_bytes();
+
+cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
+                        cudaStream_t st);
+
+// Tensor-map encoding through the driver entry point (no libcuda link dependency).
+int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err);
+
+}  // namespace corr

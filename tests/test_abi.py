@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol declared in include/*.h,
+and rejects bad arguments before touching the GPU. No compute calls (runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(corr_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1411_3751_gb300 import corr
+
+    return corr
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "corr_create" in names and "corr_dump" in names and len(names) >= 15
+    raw = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+    bound = {n for n, _, _ in lib.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_host_only_helpers(lib):
+    assert lib.corr_n_baselines(512, 2) == 32896
+    assert lib.corr_n_baselines(32, 2) == 136
+    assert lib.corr_n_baselines(7, 2) == 0
+    assert lib.corr_n_baselines(0, 1) == 0
+    fp = lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP8TC)
+    acc = 128 * 32896 * 4 * 2 * 8 + 128 * 512 * 8
+    assert fp >= acc + 128 * 8192 * 1024
+    assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP32) < fp
+    assert lib.corr_footprint_bytes(0, 1, 1, 1, 0) == 0
+    assert lib.corr_footprint_bytes(3, 1, 1, 2, 0) == 0
+    assert lib.corr_footprint_bytes(4, 1, 1, 2, 99) == 0
+    assert "sm_103a" in lib.corr_version()
+
+
+@pytest.mark.parametrize("args", [(0, 1, 1, 1), (4, 0, 1, 2), (4, 1, 0, 2), (5, 1, 1, 2), (4, 1, 1, 3), (-2, 1, 1, 1)])
+def test_create_rejects_bad_shapes(lib, args):
+    with pytest.raises(lib.CorrError) as ei:
+        lib.corr_create(*args)
+    assert "invalid shape" in str(ei.value)
+
+
+def test_null_context_errors(lib):
+    assert lib._lib.corr_set_path(None, 0) == lib.CORR_ERR_ARG
+    assert lib._lib.corr_accumulate(None, None, None) == lib.CORR_ERR_ARG
+    assert lib._lib.corr_dump(None, None, 1, 1, 0, 0, None) == lib.CORR_ERR_ARG
+    assert "NULL context" in lib.corr_last_error()
+    assert lib._lib.corr_destroy(None) == lib.CORR_OK

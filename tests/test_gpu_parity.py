@@ -1,0 +1,269 @@
+"""GPU parity: every path of libcorr, called through the C ABI, against the CPU oracle.
+
+The bar is bit-exact equality (correlation of integers is integer work). Inputs are seeded; small
+cases are generated on the host and copied to the device, the full-size case is generated on the
+device and the sampled channels are regenerated independently on the host for the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["fp32", "fp8tc"]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1411_3751_gb300 import corr, synth
+
+    assert torch.cuda.is_available()
+    return corr, synth, torch
+
+
+def _run(env, host, npol, path, blocks=1, flush=0, dump_device=True):
+    corr, _, torch = env
+    T, C, N = host.shape[0] // blocks, host.shape[1], host.shape[2]
+    with corr.Correlator(N, C, T, npol, path=path) as xc:
+        if flush:
+            xc.set_flush_period(flush)
+        for b in range(blocks):
+            xc.accumulate(torch.from_numpy(np.ascontiguousarray(host[b * T:(b + 1) * T])).cuda())
+        cross = xc.dump(corr.CORR_WHAT_CROSS, device=dump_device)
+        autos = xc.dump(corr.CORR_WHAT_AUTO, device=dump_device)
+        xc.sync()
+        assert xc.samples(corr.CORR_WHAT_CROSS) == T * blocks
+        return cross.cpu().numpy(), autos.cpu().numpy()
+
+
+def _check(env, host, npol, path, **kw):
+    want_c, want_a = oracle.correlate(host, npol, threads=8)
+    got_c, got_a = _run(env, host, npol, path, **kw)
+    assert got_c.shape == want_c.shape
+    bad = np.argwhere(got_c != want_c)
+    assert bad.size == 0, "cross mismatch at %s (got %s want %s)" % (bad[:3].tolist(), got_c[tuple(bad[0])],
+                                                                      want_c[tuple(bad[0])])
+    assert np.array_equal(got_a, want_a)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_tiny_uniform_32_inputs(env, path):
+    """N=32 (16 dual-pol stations), 8 channels, 1024 samples, uniform components: bit-exact."""
+    _, synth, _ = env
+    host = synth.generate_host(synth.Spec(kind="uniform", seed=0x14113751 + 1), 1024, 8, 32)
+    _check(env, host, 2, path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("shape", [(200, 3, 1000, 2), (6, 2, 33, 1), (130, 2, 300, 2), (96, 1, 129, 2),
+                                   (512, 2, 640, 2), (1, 1, 5, 1), (2, 1, 1, 2), (258, 2, 256, 2), (64, 3, 4096, 1)])
+def test_ragged_shapes(env, path, shape):
+    """Input counts that are not tile multiples, T not a multiple of the time granule, n_pol 1 and 2."""
+    N, C, T, npol = shape
+    _, synth, _ = env
+    host = synth.generate_host(synth.Spec(kind="gauss_tone", seed=N * 131 + T), T, C, N)
+    _check(env, host, npol, path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("byte,expect_re", [(0x88, 128), (0x77, 98)])
+def test_extremes_closed_form(env, path, byte, expect_re):
+    T, C, N = 2048, 2, 128
+    host = np.full((T, C, N), byte, dtype=np.uint8)
+    c, a = _run(env, host, 2, path)
+    assert np.all(c[..., 0] == expect_re * T) and np.all(c[..., 1] == 0)
+    assert np.all(a == expect_re * T)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_rank1_common_signal(env, path):
+    """x_m(t) = c_m s(t), s in {1, -1, i, -i}: V = T c c^H exactly (the CW-tone test of Sec. 5, exact form)."""
+    rng = np.random.default_rng(99)
+    T, C, N = 1536, 3, 96
+    cm = rng.integers(-7, 8, size=(C, N)) + 1j * rng.integers(-7, 8, size=(C, N))
+    st = np.array([1, -1, 1j, -1j])[rng.integers(0, 4, size=(T, C))]
+    x = st[:, :, None] * cm[None]
+    host = oracle.pack(np.real(x).astype(np.int64), np.imag(x).astype(np.int64))
+    c, a = _run(env, host, 2, path)
+    S = N // 2
+    for f in range(C):
+        V = T * np.outer(cm[f], np.conj(cm[f]))
+        for sa in range(0, S, 7):
+            for sc in range(0, sa + 1, 5):
+                b = sa * (sa + 1) // 2 + sc
+                for p in range(2):
+                    for q in range(2):
+                        v = V[2 * sa + p, 2 * sc + q]
+                        assert c[f, b, 2 * p + q, 0] == round(v.real) and c[f, b, 2 * p + q, 1] == round(v.imag)
+        assert np.array_equal(a[f], np.round(T * np.abs(cm[f]) ** 2).astype(np.int64))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_multiple_blocks_and_flush_periods(env, path):
+    """Linearity across accumulate calls and in-block flushes: 3 blocks == oracle on the concatenation."""
+    _, synth, _ = env
+    T, C, N = 1024, 2, 160
+    host = synth.generate_host(synth.Spec(kind="saturate", seed=4242, seg_len=256, m8_segment=2), 3 * T, C, N)
+    _check(env, host, 2, path, blocks=3)
+    _check(env, host, 2, path, blocks=3, flush=128)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_dump_formats_host_and_reset(env, path):
+    corr, synth, torch = env
+    T, C, N = 512, 2, 64
+    host = synth.generate_host(synth.Spec(kind="gauss_tone", seed=77), 2 * T, C, N)
+    want_c1, want_a1 = oracle.correlate(host[:T], 2)
+    want_c2, want_a2 = oracle.correlate(host, 2)
+    with corr.Correlator(N, C, T, 2, path=path) as xc:
+        xc.accumulate(torch.from_numpy(host[:T].copy()).cuda())
+        f32 = xc.dump(corr.CORR_WHAT_CROSS, corr.CORR_FMT_CF32, device=False)
+        nrm = xc.dump(corr.CORR_WHAT_CROSS, corr.CORR_FMT_CF32_NORM)
+        anrm = xc.dump(corr.CORR_WHAT_AUTO, corr.CORR_FMT_CF32_NORM, device=False)
+        # total-power cadence independent of the cross cadence: dump + reset the autos only
+        a1 = xc.dump(corr.CORR_WHAT_AUTO, reset=True)
+        xc.sync()
+        assert xc.samples(corr.CORR_WHAT_AUTO) == 0 and xc.samples(corr.CORR_WHAT_CROSS) == T
+        xc.accumulate(torch.from_numpy(host[T:].copy()).cuda())
+        c2 = xc.dump(corr.CORR_WHAT_CROSS, reset=True, device=False)
+        a2 = xc.dump(corr.CORR_WHAT_AUTO)
+        xc.sync()
+        assert xc.samples(corr.CORR_WHAT_CROSS) == 0
+        c3 = xc.dump(corr.CORR_WHAT_CROSS)
+        xc.sync()
+    assert np.array_equal(f32.numpy(), oracle.to_format(want_c1, oracle.FMT_CF32, T))
+    assert np.array_equal(nrm.cpu().numpy(), oracle.to_format(want_c1, oracle.FMT_CF32_NORM, T))
+    assert np.array_equal(anrm.numpy(), oracle.to_format(want_a1, oracle.FMT_CF32_NORM, T))
+    assert np.array_equal(a1.cpu().numpy(), want_a1)
+    assert np.array_equal(c2.numpy(), want_c2)
+    assert np.array_equal(a2.cpu().numpy(), want_a2 - want_a1)
+    assert np.all(c3.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("shape", [(200, 3, 1000), (512, 4, 2048), (7, 2, 3)])
+def test_autos_warp_shuffle_kernel(env, shape):
+    corr, synth, torch = env
+    N, C, T = shape
+    host = synth.generate_host(synth.Spec(kind="gauss_tone", seed=5 + N), T, C, N)
+    npol = 1 if N % 2 else 2
+    with corr.Correlator(N, C, T, npol) as xc:
+        xc.accumulate_autos(torch.from_numpy(host).cuda())
+        a = xc.dump(corr.CORR_WHAT_AUTO)
+        xc.sync()
+        assert xc.samples(corr.CORR_WHAT_AUTO) == T and xc.samples(corr.CORR_WHAT_CROSS) == 0
+    assert np.array_equal(a.cpu().numpy(), oracle.autos(host))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_accumulate_from_host_buffer(env, path):
+    corr, synth, torch = env
+    T, C, N = 3000, 4, 96
+    host = synth.generate_host(synth.Spec(kind="gauss_tone", seed=31), T, C, N)
+    want_c, want_a = oracle.correlate(host, 2, threads=8)
+    with corr.Correlator(N, C, T, 2, path=path) as xc:
+        xc.accumulate_host(torch.from_numpy(host).pin_memory())
+        c = xc.dump(corr.CORR_WHAT_CROSS, device=False)
+        a = xc.dump(corr.CORR_WHAT_AUTO, device=False)
+        xc.sync()
+    assert np.array_equal(c.numpy(), want_c) and np.array_equal(a.numpy(), want_a)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "gauss_tone", "saturate"])
+def test_device_generator_matches_host_generator(env, kind):
+    _, synth, torch = env
+    spec = synth.Spec(kind=kind, seed=123, seg_len=512, m8_segment=1)
+    T, C, N = 2048, 3, 40
+    d = synth.generate_device(spec, T, C, N, t0=4096).cpu().numpy()
+    h = synth.generate_host(spec, T, C, N, t0=4096)
+    assert np.array_equal(d, h)
+
+
+def _hermitian_from_triangle(V_cross, N, npol):
+    S = N // npol
+    Vf = np.zeros((N, N), dtype=np.complex128)
+    for sa in range(S):
+        for sc in range(sa + 1):
+            b = sa * (sa + 1) // 2 + sc
+            for p in range(npol):
+                for q in range(npol):
+                    i, j = sa * npol + p, sc * npol + q
+                    if i < j:  # XY of an auto-station: its conjugate YX fills both cells
+                        continue
+                    v = V_cross[b, p * npol + q]
+                    Vf[i, j] = v[0] + 1j * v[1]
+                    Vf[j, i] = v[0] - 1j * v[1]
+    return Vf
+
+
+def _freivalds(x_bytes, V_cross, npol, rng, chunk=16384):
+    """Check V w == sum_t x(t) (x(t)^H w) for a random small-integer w, per channel. Products run in
+    float64 BLAS on integers far below 2^53, so every step is exact."""
+    T, N = x_bytes.shape
+    Vf = _hermitian_from_triangle(V_cross, N, npol)
+    w = rng.integers(-2, 3, size=N) + 1j * rng.integers(-2, 3, size=N)
+    wr, wi = np.real(w), np.imag(w)
+    zr = np.zeros(N)
+    zi = np.zeros(N)
+    for t0 in range(0, T, chunk):
+        re, im = oracle.unpack(x_bytes[t0:t0 + chunk])
+        re = re.astype(np.float64)
+        im = im.astype(np.float64)
+        yr = re @ wr + im @ wi  # y(t) = x(t)^H w
+        yi = re @ wi - im @ wr
+        zr += re.T @ yr - im.T @ yi  # z = sum_t x(t) y(t)
+        zi += re.T @ yi + im.T @ yr
+    Vw = Vf @ w
+    return np.array_equal(Vw.real, zr) and np.array_equal(Vw.imag, zi)
+
+
+def test_full_size_512_inputs_128_channels_fp8(env):
+    """N=512, C=128, 16 blocks of 8192 samples (the benchmark's configuration and launch sequence):
+    sampled cells against the oracle on host-regenerated channels, all autos, Freivalds projections on
+    every channel, and the auto-station invariants."""
+    corr, synth, torch = env
+    N, C, T, B, npol = 512, 128, 8192, 16, 2
+    spec = synth.Spec(kind="gauss_tone", seed=0x14113751 + 2)
+    xc = corr.Correlator(N, C, T, npol, path="fp8tc")
+    buf = torch.empty((T, C, N), dtype=torch.uint8, device="cuda")
+    host_all = np.empty((B * T, C, N), dtype=np.uint8)
+    for b in range(B):
+        synth.generate_device(spec, T, C, N, t0=b * T, out=buf)
+        xc.accumulate(buf)
+        host_all[b * T:(b + 1) * T] = buf.cpu().numpy()
+    cross = xc.dump(corr.CORR_WHAT_CROSS, device=False)
+    autos = xc.dump(corr.CORR_WHAT_AUTO, device=False)
+    xc.sync()
+    xc.close()
+    cross, autos = cross.numpy(), autos.numpy()
+    rng = np.random.default_rng(2024)
+    # 1) sampled channels regenerated on the host; generator agreement; oracle cells
+    for f in (0, 45, 127):
+        hf = synth.generate_host(spec, B * T, C, N, c_range=(f, f + 1))
+        assert np.array_equal(hf[:, 0], host_all[:, f])
+        cells, idx = [], []
+        for _ in range(96):
+            sa = int(rng.integers(0, N // 2))
+            sc = int(rng.integers(0, sa + 1))
+            p, q = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+            cells.append((0, 2 * sa + p, 2 * sc + q))
+            idx.append((sa * (sa + 1) // 2 + sc, 2 * p + q))
+        got = oracle.cells(hf, cells)
+        for k, (b, pq) in enumerate(idx):
+            assert tuple(cross[f, b, pq]) == tuple(got[k]), (f, b, pq)
+    # 2) every channel: oracle autos and a Freivalds projection of the full Hermitian matrix
+    for f in range(C):
+        xf = np.ascontiguousarray(host_all[:, f])
+        assert np.array_equal(autos[f], oracle.autos(xf[:, None, :])[0]), "autos mismatch on channel %d" % f
+        assert _freivalds(xf, cross[f], npol, rng), "Freivalds failed on channel %d" % f
+    # 3) auto-station invariants
+    S = N // 2
+    diag = np.array([s * (s + 1) // 2 + s for s in range(S)])
+    assert np.array_equal(cross[:, diag, 0, 0], autos[:, 0::2]) and np.array_equal(cross[:, diag, 3, 0], autos[:, 1::2])
+    assert np.array_equal(cross[:, diag, 2, 0], cross[:, diag, 1, 0])
+    assert np.array_equal(cross[:, diag, 2, 1], -cross[:, diag, 1, 1])

@@ -207,7 +207,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp32"])
+    ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp8tc_fused", "fp32"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp32-steps", type=int, default=2)
@@ -265,6 +265,7 @@ def main():
     xeng_ms, xeng_n = xc.profile_read(corr.CORR_KERNEL_XENG)
     unpack_ms, unpack_n = xc.profile_read(corr.CORR_KERNEL_UNPACK)
     dump_ms, dump_n = xc.profile_read(corr.CORR_KERNEL_DUMP)
+    autos_ms, autos_n = xc.profile_read(corr.CORR_KERNEL_AUTOS)
     xc.profile(False)
     clk = clocks.stop()
     xc.sync()
@@ -278,7 +279,7 @@ def main():
     peaks, peak_src = load_peaks()
     per_launch_ms = xeng_ms / max(1, xeng_n)
     flops_launch = 8.0 * useful_cmacs(N_IN, N_CHAN, T_BLOCK)
-    if args.path == "fp8tc":
+    if args.path.startswith("fp8tc"):
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_note = "%s bf16 sustained x 2 (nominal fp8/bf16 ratio)" % peak_src
         bound = "tensor"
@@ -288,7 +289,7 @@ def main():
         bound = "alu"
     achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "f8_xeng_kernel" if args.path == "fp8tc" else "xeng_fp32_kernel",
+            "traffic": None, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel"}.get(args.path, "xeng_fp32_kernel"),
             "peak_source": peak_note, "launch_ms": per_launch_ms,
             "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop" % flops_launch}
 
@@ -323,7 +324,7 @@ def main():
 
     # same-GPU FP32 path on the same workload (comparison leg of the metric)
     fp32 = None
-    if args.path == "fp8tc" and args.fp32_steps > 0:
+    if args.path.startswith("fp8tc") and args.fp32_steps > 0:
         xc.set_path("fp32")
         step()
         torch.cuda.synchronize()
@@ -345,19 +346,19 @@ def main():
         cpu = cpu_baseline()
 
     if rank == 0:
-        launches_per_step = N_BLOCKS * (2 if args.path == "fp8tc" else 1) + 2
+        launches_per_step = N_BLOCKS * {"fp8tc": 3, "fp8tc_fused": 2}.get(args.path, 1) + 2
         line = {
             "metric": METRIC, "value": value, "unit": "Tera-CMAC/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3" if args.path == "fp8tc" else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "e4m3" if args.path.startswith("fp8tc") else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN, "n_time_per_block": T_BLOCK,
                        "blocks_per_step": N_BLOCKS, "n_pol": N_POL, "path": args.path,
                        "l2": "inputs 8 GiB > L2, no flush needed", "parallelism": "channels per GPU (replicas)"},
             "real_time_factor": rtf,
             "roofline": roof,
             "kernel_ms_per_step": {"xeng": xeng_ms / args.steps, "unpack": unpack_ms / args.steps,
-                                   "dump": dump_ms / args.steps},
-            "gpu_launches": (xeng_n + unpack_n + dump_n),
+                                   "autos_side_stream": autos_ms / args.steps, "dump": dump_ms / args.steps},
+            "gpu_launches": (xeng_n + unpack_n + dump_n + autos_n),
             "gpu_launches_per_step": launches_per_step,
             "clocks": clk,
             "e2e": e2e,

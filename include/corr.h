@@ -60,7 +60,11 @@ typedef enum corr_status {
 typedef enum corr_path {
   CORR_PATH_AUTO = 0,  /* fastest available: FP8 tensor path on sm_103a */
   CORR_PATH_FP32 = 1,  /* FP32 FMA on CUDA cores (the arithmetic the paper's K20X X-engine used, Sec. 2.5) */
-  CORR_PATH_FP8TC = 3  /* tcgen05 kind::f8f6f4 e4m3 operands, FP32 accumulation in TMEM */
+  CORR_PATH_FP8TC = 3, /* tcgen05 kind::f8f6f4 (e4m3 operands, FP32 accumulation in TMEM): an
+                          unpack pass builds the operand in device scratch, a TMA-fed persistent
+                          kernel multiplies; the total-power kernel runs alongside. The default. */
+  CORR_PATH_FP8TC_FUSED = 4 /* same arithmetic with the unpack done inside the X-engine by converter
+                               warps (no scratch; slower on this input layout, kept for comparison) */
 } corr_path;
 
 typedef enum corr_what { CORR_WHAT_CROSS = 1, CORR_WHAT_AUTO = 2 } corr_what;

@@ -12,63 +12,104 @@ __device__ __forceinline__ int power_of(unsigned b) {
 }
 
 // Autocorrelations A[f][n] += sum_t |x_{f,n}(t)|^2 (Sec. 2.6: total power of selected inputs at a
-// high cadence). One block of 4 warps per (channel, group of 32 inputs). Lane l of a warp reads
-// the 4 inputs 4 (l % 8) .. +3 at time offset l / 8, so each warp covers 32 inputs x 4 samples per
-// step and each sample byte is read once. Per-thread int32 partials are reduced over the four time
-// lanes with warp shuffles, then over the 4 warps through shared memory, and added to int64.
+// high cadence), and optionally the offset sums s[f][n] += sum_t (x + 8 + 8i) needed to map the
+// tensor path's offset-domain products back to V (see the fused X-engine). One block of 4 warps per
+// (channel, group of 32 inputs). Lane l of a warp reads the 4 inputs 4 (l % 8) .. +3 at time offset
+// l / 8, so each warp covers 32 inputs x 4 samples per step and each sample byte is read once.
+// Per-thread int32 partials are reduced over the four time lanes with warp shuffles, then over the
+// 4 warps through shared memory, and added to int64.
 constexpr int AW = 4;
 
 __global__ void __launch_bounds__(AW * 32) autos_kernel(const uint8_t* __restrict__ in, int N, int C, int T,
-                                                        long long* __restrict__ autos) {
+                                                        long long* __restrict__ autos, long long* __restrict__ soff) {
   const int f = blockIdx.y;
   const int n0 = blockIdx.x * 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sub = lane & 7, toff = lane >> 3;  // inputs n0 + 4 sub .. +3, time offset 0..3
-  int acc[4] = {0, 0, 0, 0};
-  long long acc64[4] = {0, 0, 0, 0};
+  int acc[4] = {0, 0, 0, 0}, sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
+  long long acc64[4] = {0, 0, 0, 0}, sr64[4] = {0, 0, 0, 0}, si64[4] = {0, 0, 0, 0};
   int since = 0;
   for (int t = warp * 4 + toff; t < T; t += AW * 4) {
     const uint8_t* row = in + ((size_t)t * C + f) * N + n0 + 4 * sub;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (n0 + 4 * sub + q < N) acc[q] += power_of(row[q]);
+      if (n0 + 4 * sub + q < N) {
+        const unsigned b = row[q];
+        acc[q] += power_of(b);
+        sr[q] += (int)((b >> 4) ^ 8u);   // Re + 8
+        si[q] += (int)((b & 15u) ^ 8u);  // Im + 8
+      }
     if (++since == (1 << 20)) {  // int32 partials stay below 128 * 2^20
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc64[q] += acc[q];
-        acc[q] = 0;
+        sr64[q] += sr[q];
+        si64[q] += si[q];
+        acc[q] = sr[q] = si[q] = 0;
       }
       since = 0;
     }
   }
+  __shared__ long long part[3][AW][32];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    long long v = acc64[q] + acc[q];
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    acc64[q] = v;
-  }
-  __shared__ long long part[AW][32];
-  if (toff == 0) {
+    long long v[3] = {acc64[q] + acc[q], sr64[q] + sr[q], si64[q] + si[q]};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) part[warp][4 * sub + q] = acc64[q];
+    for (int k = 0; k < 3; ++k) {
+      v[k] += __shfl_xor_sync(0xffffffffu, v[k], 8);
+      v[k] += __shfl_xor_sync(0xffffffffu, v[k], 16);
+      if (toff == 0) part[k][warp][4 * sub + q] = v[k];
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
     const int n = n0 + threadIdx.x;
-    long long s = 0;
+    long long sum[3] = {0, 0, 0};
 #pragma unroll
-    for (int w = 0; w < AW; ++w) s += part[w][threadIdx.x];
-    if (n < N) autos[(long long)f * N + n] += s;
+    for (int w = 0; w < AW; ++w)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sum[k] += part[k][w][threadIdx.x];
+    if (n < N) {
+      autos[(long long)f * N + n] += sum[0];
+      if (soff) {
+        soff[((long long)f * N + n) * 2] += sum[1];
+        soff[((long long)f * N + n) * 2 + 1] += sum[2];
+      }
+    }
   }
 }
 
 // Dump: out[k] = fmt(acc[k]). CI64 copies, CF32 rounds to nearest float, CF32_NORM divides by the
-// sample count in double and rounds to float.
+// sample count in double and rounds to float. Contributions of the tensor path are held in the
+// offset domain (u = x + 8 + 8i) and are mapped back here:
+//   V = Vu - (8 - 8i) s_a - (8 + 8i) conj(s_c) + 128 T_off,   A = Au - 16 (Re s + Im s) + 128 T_off
+// (s = per-input offset sums and T_off = samples accumulated through that path, per cadence).
+__device__ __forceinline__ long long corrected(const long long* __restrict__ acc, long long k, const Shape2& g) {
+  long long v = acc[k];
+  if (g.soff == nullptr || g.t_off == 0) return v;
+  if (g.autos) return v - 16 * (g.soff[2 * k] + g.soff[2 * k + 1]) + 128 * g.t_off;  // A = Au - 16 (Re s + Im s) + 128 T
+  const long long cell = k >> 1;
+  const int comp = (int)(k & 1);
+  const int pidx = (int)(cell % g.P);
+  const long long fb = cell / g.P;
+  const long long b = fb % g.Bs;
+  const long long f = fb / g.Bs;
+  long long sa = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while (sa * (sa + 1) / 2 > b) --sa;
+  while ((sa + 1) * (sa + 2) / 2 <= b) ++sa;
+  const long long sc = b - sa * (sa + 1) / 2;
+  const long long a = sa * g.npol + pidx / g.npol;
+  const long long c = sc * g.npol + pidx % g.npol;
+  const long long* s_a = g.soff + (f * g.N + a) * 2;
+  const long long* s_c = g.soff + (f * g.N + c) * 2;
+  if (comp == 0) return v - 8 * (s_a[0] + s_a[1] + s_c[0] + s_c[1]) + 128 * g.t_off;
+  return v - 8 * (s_a[1] - s_a[0] + s_c[0] - s_c[1]);
+}
+
 __global__ void dump_kernel(const long long* __restrict__ acc, long long n, void* __restrict__ out, int fmt,
-                            long long n_samples) {
+                            long long n_samples, long long k_base, Shape2 g) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const long long v = acc[k];
+    const long long v = corrected(acc, k_base + k, g);
     if (fmt == CORR_FMT_CI64) {
       static_cast<long long*>(out)[k] = v;
     } else if (fmt == CORR_FMT_CF32) {
@@ -81,19 +122,20 @@ __global__ void dump_kernel(const long long* __restrict__ acc, long long n, void
 
 }  // namespace
 
-cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long long* d_autos, cudaStream_t st) {
+cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long long* d_autos, long long* d_soff,
+                         cudaStream_t st) {
   if (T_blk == 0) return cudaSuccess;
   dim3 grid((s.N + 31) / 32, s.C);
-  autos_kernel<<<grid, AW * 32, 0, st>>>(d_in, s.N, s.C, T_blk, d_autos);
+  autos_kernel<<<grid, AW * 32, 0, st>>>(d_in, s.N, s.C, T_blk, d_autos, d_soff);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
-                        cudaStream_t st) {
+                        long long k_base, const Shape2& g, cudaStream_t st) {
   if (n_elems == 0) return cudaSuccess;
   long long blocks = (n_elems + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  dump_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, n_elems, d_out, fmt, n_samples);
+  dump_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, n_elems, d_out, fmt, n_samples, k_base, g);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,8 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(CORR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr size_t kStageBytes = 64ull << 20;  // host-transfer staging buffer, x2
+constexpr size_t kStageBytes = 64ull << 20;     // host-dump staging buffer, x2
+constexpr size_t kMaxInStage = 512ull << 20;    // host-input staging buffer (per buffer), x2
 
 struct Layout {
   Shape s;
@@ -66,9 +67,14 @@ Layout make_layout(int N, int C, int T, int npol) {
   return L;
 }
 
+size_t in_stage_bytes(const Layout& L) {
+  const size_t block = (size_t)L.s.T * L.s.C * L.s.N;
+  return block < kMaxInStage ? block : kMaxInStage;
+}
+
 size_t footprint(const Layout& L, int path) {
-  size_t b = (size_t)(L.cross_elems + L.autos_elems) * 8 + 256;
-  b += 2 * kStageBytes;
+  size_t b = (size_t)(L.cross_elems + L.autos_elems) * 8 + (size_t)L.autos_elems * 32 + 256;
+  b += 2 * kStageBytes + 2 * in_stage_bytes(L);
   if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += L.op_bytes;
   const long long nb = (L.s.N + 63) / 64;
   b += (size_t)(nb * (nb + 1) / 2) * sizeof(int2) + (size_t)(nb * 8 + 8) * sizeof(F8Tile);
@@ -126,6 +132,10 @@ struct corr_ctx {
   int num_sms;
   long long* d_cross;
   long long* d_autos;
+  long long* d_soff;       // [C][N][2] offset sums of the tensor paths (cross cadence)
+  long long* d_soff_auto;  // same, total-power cadence
+  long long n_off;         // samples accumulated through a tensor path since the cross reset
+  long long n_off_auto;    // same, since the autos reset
   int* d_err;
   uint8_t* d_op;
   CUtensorMap tmap;
@@ -133,7 +143,13 @@ struct corr_ctx {
   int n_tiles32;
   F8Tile* d_tiles8;
   int n_tiles8;
-  void* d_stage[2];
+  void* d_stage[2];      // host dumps
+  void* d_in_stage[2];   // host inputs
+  size_t in_stage;
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_copied[2], ev_free[2];
+  bool free_recorded[2];
+  int next_in;
   long long n_cross;
   long long n_auto;
 };
@@ -141,6 +157,10 @@ struct corr_ctx {
 namespace {
 
 int resolved_path(const corr_ctx* c) { return c->path == CORR_PATH_AUTO ? CORR_PATH_FP8TC : c->path; }
+
+bool valid_path(int path) {
+  return path == CORR_PATH_AUTO || path == CORR_PATH_FP32 || path == CORR_PATH_FP8TC || path == CORR_PATH_FP8TC_FUSED;
+}
 
 int flush_for(const corr_ctx* c, int path) {
   if (c->flush_len > 0) {
@@ -187,12 +207,21 @@ void free_ctx(corr_ctx* c) {
     for (cudaEvent_t e : c->timers[k].ev) cudaEventDestroy(e);
   cudaFree(c->d_cross);
   cudaFree(c->d_autos);
+  cudaFree(c->d_soff);
+  cudaFree(c->d_soff_auto);
   cudaFree(c->d_err);
   cudaFree(c->d_op);
   cudaFree(c->d_tiles32);
   cudaFree(c->d_tiles8);
   cudaFree(c->d_stage[0]);
   cudaFree(c->d_stage[1]);
+  cudaFree(c->d_in_stage[0]);
+  cudaFree(c->d_in_stage[1]);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+    if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
 
@@ -207,16 +236,45 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
     timer_end(c, CORR_KERNEL_XENG, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "fp32 x-engine launch");
   } else {
+    // tensor paths: one pass builds the operand (two-pass path) and the per-input offset sums for
+    // both cadences; the X-engine adds the offset-domain products and their diagonal.
     const int T_run = (int)round_up(T_blk, kF8Kt);
+    const bool two_pass = path == CORR_PATH_FP8TC;
     bool tb = timer_begin(c, CORR_KERNEL_UNPACK, st);
-    e = launch_f8_unpack(c->L.s, d_in, T_blk, T_run, c->L.T_pad, c->L.R, c->d_op, st);
+    e = launch_f8_prep(c->L.s, d_in, T_blk, T_run, c->L.T_pad, c->L.R, two_pass ? c->d_op : nullptr, c->d_soff,
+                       c->d_soff_auto, st);
     timer_end(c, CORR_KERNEL_UNPACK, st, tb);
-    if (e != cudaSuccess) return cuda_fail(e, "fp8 unpack launch");
+    if (e != cudaSuccess) return cuda_fail(e, "operand build launch");
     tb = timer_begin(c, CORR_KERNEL_XENG, st);
-    e = launch_f8_xeng(c->L.s, &c->tmap, T_run, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
-                       c->num_sms, st);
+    if (two_pass)
+      e = launch_f8_xeng(c->L.s, &c->tmap, T_run, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
+                         c->num_sms, st);
+    else
+      e = launch_f8_fused(c->L.s, d_in, T_blk, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
+                          c->num_sms, st);
     timer_end(c, CORR_KERNEL_XENG, st, tb);
-    if (e != cudaSuccess) return cuda_fail(e, "fp8 x-engine launch");
+    if (e != cudaSuccess) return cuda_fail(e, "tensor x-engine launch");
+    c->n_off += T_blk;
+    c->n_off_auto += T_blk;
+  }
+  return CORR_OK;
+}
+
+// The two-pass tensor path's operand scratch and its TMA tensor map.
+int ensure_operand_scratch(corr_ctx* c) {
+  if (c->d_op) return CORR_OK;
+  if (cudaMalloc(&c->d_op, c->L.op_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_op = nullptr;
+    return fail(CORR_ERR_OOM, "operand scratch allocation failed");
+  }
+  cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
+  std::string err;
+  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R, c->L.T_pad, c->L.s.C, &err) != 0) {
+    cudaFree(c->d_op);
+    c->d_op = nullptr;
+    return fail(CORR_ERR_CUDA, err);
   }
   return CORR_OK;
 }
@@ -237,7 +295,7 @@ long long corr_n_baselines(int n_inputs, int n_pol) {
 
 size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int n_pol, int path) {
   const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
-  if (!L.ok || (path != CORR_PATH_AUTO && path != CORR_PATH_FP32 && path != CORR_PATH_FP8TC)) return 0;
+  if (!L.ok || !valid_path(path)) return 0;
   return footprint(L, path);
 }
 
@@ -282,12 +340,21 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
   c->n_tiles8 = (int)t8.size();
   bool ok = cudaMalloc(&c->d_cross, (size_t)L.cross_elems * 8) == cudaSuccess &&
             cudaMalloc(&c->d_autos, (size_t)L.autos_elems * 8) == cudaSuccess &&
+            cudaMalloc(&c->d_soff, (size_t)L.autos_elems * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_soff_auto, (size_t)L.autos_elems * 16) == cudaSuccess &&
             cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&c->d_op, L.op_bytes) == cudaSuccess &&
             cudaMalloc(&c->d_tiles32, t32.size() * sizeof(int2)) == cudaSuccess &&
             cudaMalloc(&c->d_tiles8, t8.size() * sizeof(F8Tile)) == cudaSuccess &&
             cudaMalloc(&c->d_stage[0], kStageBytes) == cudaSuccess &&
-            cudaMalloc(&c->d_stage[1], kStageBytes) == cudaSuccess;
+            cudaMalloc(&c->d_stage[1], kStageBytes) == cudaSuccess &&
+            cudaMalloc(&c->d_in_stage[0], in_stage_bytes(L)) == cudaSuccess &&
+            cudaMalloc(&c->d_in_stage[1], in_stage_bytes(L)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_copied[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_copied[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_free[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming) == cudaSuccess;
+  c->in_stage = in_stage_bytes(L);
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -296,7 +363,9 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
   }
   ok = cudaMemset(c->d_cross, 0, (size_t)L.cross_elems * 8) == cudaSuccess &&
        cudaMemset(c->d_autos, 0, (size_t)L.autos_elems * 8) == cudaSuccess &&
-       cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess && cudaMemset(c->d_op, 0, L.op_bytes) == cudaSuccess &&
+       cudaMemset(c->d_soff, 0, (size_t)L.autos_elems * 16) == cudaSuccess &&
+       cudaMemset(c->d_soff_auto, 0, (size_t)L.autos_elems * 16) == cudaSuccess &&
+       cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
        cudaMemcpy(c->d_tiles32, t32.data(), t32.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d_tiles8, t8.data(), t8.size() * sizeof(F8Tile), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
@@ -305,10 +374,10 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
     cuda_fail(e, "corr_create: initialisation");
     return nullptr;
   }
-  std::string err;
-  if (encode_op_tensor_map(&c->tmap, c->d_op, L.R, L.T_pad, L.s.C, &err) != 0) {
+  if (ensure_operand_scratch(c) != CORR_OK) {
+    const std::string msg = g_err;
     free_ctx(c);
-    fail(CORR_ERR_CUDA, "corr_create: " + err);
+    fail(CORR_ERR_OOM, "corr_create: " + msg);
     return nullptr;
   }
   return c;
@@ -316,8 +385,11 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
 
 int corr_set_path(corr_ctx* c, int path) {
   if (!c) return fail(CORR_ERR_ARG, "corr_set_path: NULL context");
-  if (path != CORR_PATH_AUTO && path != CORR_PATH_FP32 && path != CORR_PATH_FP8TC)
-    return fail(CORR_ERR_ARG, "corr_set_path: unknown path " + std::to_string(path));
+  if (!valid_path(path)) return fail(CORR_ERR_ARG, "corr_set_path: unknown path " + std::to_string(path));
+  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) {
+    const int rc = ensure_operand_scratch(c);
+    if (rc != CORR_OK) return rc;
+  }
   c->path = path;
   return CORR_OK;
 }
@@ -349,18 +421,30 @@ int corr_accumulate_host(corr_ctx* c, const void* h_samples, void* stream) {
   if (!h_samples) return fail(CORR_ERR_ARG, "corr_accumulate_host: NULL samples");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t row = (size_t)c->L.s.C * c->L.s.N;  // bytes per time sample
-  long long slice = (long long)(kStageBytes / row);
-  if (slice >= kF8Kt) slice = slice / kF8Kt * kF8Kt;
+  long long slice = (long long)(c->in_stage / row);
+  if (slice >= c->L.s.T) slice = c->L.s.T;
+  else if (slice >= kF8Kt) slice = slice / kF8Kt * kF8Kt;
   if (slice < 1) return fail(CORR_ERR_ARG, "corr_accumulate_host: one time sample exceeds the staging buffer");
   const uint8_t* src = static_cast<const uint8_t*>(h_samples);
-  int buf = 0;
+  // Double-buffered: the copy stream fills staging buffer k while the caller's stream computes on
+  // the other; events order reuse of a buffer after the kernels that read it.
   for (long long t0 = 0; t0 < c->L.s.T; t0 += slice) {
     const int n = (int)((c->L.s.T - t0) < slice ? (c->L.s.T - t0) : slice);
-    cudaError_t e = cudaMemcpyAsync(c->d_stage[buf], src + (size_t)t0 * row, (size_t)n * row, cudaMemcpyHostToDevice, st);
+    const int buf = c->next_in;
+    c->next_in ^= 1;
+    cudaError_t e = cudaSuccess;
+    if (c->free_recorded[buf]) e = cudaStreamWaitEvent(c->copy_stream, c->ev_free[buf], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_in_stage[buf], src + (size_t)t0 * row, (size_t)n * row, cudaMemcpyHostToDevice,
+                          c->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_copied[buf], c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_copied[buf], 0);
     if (e != cudaSuccess) return cuda_fail(e, "corr_accumulate_host: copy");
-    const int rc = accumulate_device(c, static_cast<const uint8_t*>(c->d_stage[buf]), n, st);
+    const int rc = accumulate_device(c, static_cast<const uint8_t*>(c->d_in_stage[buf]), n, st);
     if (rc != CORR_OK) return rc;
-    buf ^= 1;
+    e = cudaEventRecord(c->ev_free[buf], st);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_accumulate_host: event");
+    c->free_recorded[buf] = true;
   }
   c->n_cross += c->L.s.T;
   c->n_auto += c->L.s.T;
@@ -371,7 +455,8 @@ int corr_accumulate_autos(corr_ctx* c, const void* d_samples, void* stream) {
   if (!c) return fail(CORR_ERR_ARG, "corr_accumulate_autos: NULL context");
   if (!d_samples) return fail(CORR_ERR_ARG, "corr_accumulate_autos: NULL samples");
   const bool tb = timer_begin(c, CORR_KERNEL_AUTOS, (cudaStream_t)stream);
-  cudaError_t e = launch_autos(c->L.s, static_cast<const uint8_t*>(d_samples), c->L.s.T, c->d_autos, (cudaStream_t)stream);
+  cudaError_t e = launch_autos(c->L.s, static_cast<const uint8_t*>(d_samples), c->L.s.T, c->d_autos, nullptr,
+                               (cudaStream_t)stream);
   timer_end(c, CORR_KERNEL_AUTOS, (cudaStream_t)stream, tb);
   if (e != cudaSuccess) return cuda_fail(e, "corr_accumulate_autos: launch");
   c->n_auto += c->L.s.T;
@@ -384,13 +469,17 @@ int corr_reset(corr_ctx* c, int what, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (what & CORR_WHAT_CROSS) {
     cudaError_t e = cudaMemsetAsync(c->d_cross, 0, (size_t)c->L.cross_elems * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_soff, 0, (size_t)c->L.autos_elems * 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "corr_reset");
     c->n_cross = 0;
+    c->n_off = 0;
   }
   if (what & CORR_WHAT_AUTO) {
     cudaError_t e = cudaMemsetAsync(c->d_autos, 0, (size_t)c->L.autos_elems * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_soff_auto, 0, (size_t)c->L.autos_elems * 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "corr_reset");
     c->n_auto = 0;
+    c->n_off_auto = 0;
   }
   return CORR_OK;
 }
@@ -406,10 +495,18 @@ int corr_dump(corr_ctx* c, void* out, int is_device_ptr, int what, int fmt, int 
   const long long n = what == CORR_WHAT_CROSS ? c->L.cross_elems : c->L.autos_elems;
   const long long ns = what == CORR_WHAT_CROSS ? c->n_cross : c->n_auto;
   const size_t esz = fmt == CORR_FMT_CI64 ? 8 : 4;
+  Shape2 g;
+  g.N = c->L.s.N;
+  g.npol = c->L.s.npol;
+  g.P = c->L.s.P;
+  g.Bs = c->L.s.Bs;
+  g.soff = what == CORR_WHAT_CROSS ? c->d_soff : c->d_soff_auto;
+  g.t_off = what == CORR_WHAT_CROSS ? c->n_off : c->n_off_auto;
+  g.autos = what == CORR_WHAT_AUTO ? 1 : 0;
   cudaError_t e;
   if (is_device_ptr) {
     const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
-    e = launch_dump(acc, n, out, fmt, ns, st);
+    e = launch_dump(acc, n, out, fmt, ns, 0, g, st);
     timer_end(c, CORR_KERNEL_DUMP, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "corr_dump: launch");
   } else {
@@ -418,7 +515,7 @@ int corr_dump(corr_ctx* c, void* out, int is_device_ptr, int what, int fmt, int 
     for (long long k = 0; k < n; k += per) {
       const long long m = (n - k) < per ? (n - k) : per;
       const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
-      e = launch_dump(acc + k, m, c->d_stage[buf], fmt, ns, st);
+      e = launch_dump(acc, m, c->d_stage[buf], fmt, ns, k, g, st);
       timer_end(c, CORR_KERNEL_DUMP, st, tb);
       if (e != cudaSuccess) return cuda_fail(e, "corr_dump: launch");
       e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + (size_t)k * esz, c->d_stage[buf], (size_t)m * esz,

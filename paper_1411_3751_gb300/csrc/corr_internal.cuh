@@ -17,16 +17,26 @@ namespace corr {
 //   cross[C][B_s][P][2]   exactly the public cross layout (corr.h), P = n_pol^2
 //   autos[C][N]
 // FP8 tensor path scratch (e4m3 operand, rebuilt by every corr_accumulate):
-//   op[C][T_pad][R]       R = round_up(2N, 128) operand rows per channel (row 2n = Re x_n,
-//                         row 2n + 1 = Im x_n, zero beyond 2N), T_pad = round_up(T, 128) time
-//                         columns (zero beyond T). Time is the contraction (K) dimension and the
-//                         rows are contiguous, i.e. an MN-major operand for the tensor cores.
+//   op[C][T_pad][R]       R = round_up(2N, 128) operand rows per channel in groups of 8 (Re of 4
+//                         inputs, Im of the same 4; offset encoding of f8_common.cuh; zero beyond
+//                         the last input), T_pad = round_up(T, 128) time columns (zero beyond T).
+//                         Time is the contraction (K) dimension and the rows are contiguous, i.e.
+//                         an MN-major operand for the tensor cores.
 
 struct Shape {
   int N, C, T, npol;
   int S;        // stations
   long long Bs; // station pairs
   int P;        // products per pair
+};
+
+// Offset-domain correction parameters for dumps (soff == nullptr: no correction).
+struct Shape2 {
+  int N, npol, P;
+  long long Bs;
+  const long long* soff;  // [C][N][2] offset sums of the tensor path
+  long long t_off;        // samples accumulated through the tensor path
+  int autos;              // 1: the accumulator is autos[C][N], else cross[C][B_s][P][2]
 };
 
 // FP8 path tile: c-side block of 64 inputs (128 operand rows, the MMA's M), a-side block starting
@@ -55,20 +65,34 @@ inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m
 cudaError_t launch_fp32(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const int2* d_tiles,
                         int n_tiles, long long* d_cross, long long* d_autos, cudaStream_t st);
 
-cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long long* d_autos, cudaStream_t st);
+// Autos (+ offset sums when d_soff != nullptr).
+cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long long* d_autos, long long* d_soff,
+                         cudaStream_t st);
 
-// T_blk valid samples; T_run = round_up(T_blk, kF8Kt) samples written; T_stride = op samples per channel.
-cudaError_t launch_f8_unpack(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
-                             uint8_t* d_op, cudaStream_t st);
+// Fused unpack + tcgen05 X-engine (offset-domain products into d_cross, diagonal into d_autos).
+cudaError_t launch_f8_fused(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const F8Tile* d_tiles,
+                            int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
+                            cudaStream_t st);
 
+// Operand build (d_op may be null) + per-input offset sums added to d_s1 and d_s2 (either may be
+// null). T_blk valid samples; T_run = round_up(T_blk, kF8Kt) samples written; T_stride = op samples
+// per channel.
+cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
+                           uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st);
+
+// Offset-domain products into d_cross, their diagonal into d_autos.
 cudaError_t launch_f8_xeng(const Shape& s, const CUtensorMap* tmap, int T_run, int flush_len, const F8Tile* d_tiles,
                            int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
                            cudaStream_t st);
 
 size_t f8_smem_bytes();
 
+// Dump elements [k_base, k_base + n_elems) of an accumulator (cross: corrected with g).
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
-                        cudaStream_t st);
+                        long long k_base, const Shape2& g, cudaStream_t st);
+
+// Thread-local message returned by corr_last_error().
+void set_last_error(const std::string& msg);
 
 // Tensor-map encoding through the driver entry point (no libcuda link dependency).
 int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err);

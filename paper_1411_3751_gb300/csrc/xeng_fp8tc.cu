@@ -1,116 +1,132 @@
-// FP8 tensor-core X-engine (tcgen05, kind::f8f6f4, e4m3 operands, FP32 accumulation in TMEM).
+// Two-pass FP8 tensor-core X-engine (tcgen05, kind::f8f6f4, e4m3 operands, FP32 accumulation in
+// TMEM). Operand encoding, row order and epilogue: f8_common.cuh.
 //
-// Real-valued formulation of the complex Hermitian rank-T update: per channel f the operand R_f has
-// rows 2n = Re x_n and 2n + 1 = Im x_n and one column per time sample, and G_f = R_f R_f^T gives
-//   Re V[a, c] = G[2a, 2c] + G[2a+1, 2c+1],   Im V[a, c] = G[2a+1, 2c] - G[2a, 2c+1]
-// (V = sum_t x x^H, the X-engine product of Sec. 2.5). Integers in [-8, 7] are exact in e4m3 and
-// every product is an integer of magnitude <= 64, so the FP32 tensor-core sums are exact while they
-// stay below 2^24, i.e. for up to 65536 samples per flush (flushed to int64 in the epilogue).
-//
-// Two kernels:
-//  * f8_unpack: packed bytes in[T][C][N] -> op[C][T_pad][R] e4m3 (MN-major operand, rows contiguous).
+//  * f8_prep: packed bytes in[T][C][N] -> op[C][T_pad][R] (offset e4m3 bytes, group row order,
+//    MN-major: one contiguous row of R bytes per channel and sample) plus the per-input offset sums.
+//    Streams through HBM.
 //  * f8_xeng: persistent, one CTA per SM, warp-specialised:
 //      warp 0      TMA producer: 128-row x 128-sample boxes of op into a 4-stage smem ring
 //      warp 1      TMEM allocator + single-thread MMA issuer (M = 128 c-side rows, N = 128 or 256
 //                  a-side rows, K = 32 samples per instruction), 2 TMEM accumulators of 256 columns
-//      warps 2-5   epilogue: tcgen05.ld, complex combine across lane pairs, FP32 -> int64, add to
-//                  the cross / auto accumulators (each output cell is owned by one thread per launch)
+//      warps 2-9   epilogue: drain of one accumulator while the MMAs fill the other
 //    Work item = (channel, triangle tile); tiles cover only station pairs a >= c (triangle-only
 //    scheduling), with half-width tiles on the diagonal to cut wasted products.
 #include <cstdio>
 
 #include "corr_internal.cuh"
-#include "ptx_sm100.cuh"
+#include "f8_common.cuh"
 
 namespace corr {
 namespace {
 
-constexpr int KT = kF8Kt;
-constexpr int STAGES = kF8Stages;
-constexpr int A_BYTES = 128 * KT;  // 128 c-side operand rows x 128 samples
-constexpr int B_ATOM = 128 * KT;   // one 128-row MN atom of the a-side operand
+using namespace f8;
+
 constexpr int B_BYTES = 2 * B_ATOM;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t ACC_COLS = 256;
-constexpr uint64_t WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+constexpr int NUM_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int EPI_THREADS = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
-// e4m3 byte of the integer value of a 4-bit two's-complement nibble (OCP FP8 E4M3: 1 sign bit,
-// 4 exponent bits with bias 7, 3 mantissa bits). Small integers are normal numbers:
-// |v| = 2^e (1 + m / 8).
-__host__ __device__ constexpr uint32_t e4m3_of_int(int v) {
-  if (v == 0) return 0u;
-  const uint32_t sign = v < 0 ? 0x80u : 0u;
-  const int mag = v < 0 ? -v : v;
-  int e = 0;
-  while ((mag >> (e + 1)) != 0) ++e;
-  const uint32_t mant = (uint32_t)(((mag << 3) >> e) & 7);
-  return sign | ((uint32_t)(e + 7) << 3) | mant;
-}
-static_assert(e4m3_of_int(1) == 0x38 && e4m3_of_int(7) == 0x4E && e4m3_of_int(-8) == 0xD0, "e4m3 encoding");
+// Operand build + offset sums, one pass over the input (the paper's CPU "unpack" stage, Sec. 2.4,
+// done on the GPU). A unit = 16 inputs (32 operand rows) of one (f, t). Lane l of a warp takes unit
+// 8 blockIdx.x + (l % 8) at time offset l / 8, so a warp reads 8 units (128 inputs) of 4 samples and
+// the 8 warps of a block cover 32 samples per step; blockIdx.z splits the time range.
+//  * op (if not null): op[f][t][r] for t < T_run (zero rows for t >= T and inputs >= N);
+//  * s1, s2 (if not null): per-input offset sums sum_t (x + 8 + 8i) over t < T, added to both
+//    (the cross-cadence and the total-power-cadence copies). Per-thread sums live in 16-bit lanes of
+//    packed words (at most 15 per sample, <= 2048 samples per thread), are reduced over the four
+//    time lanes of a warp with shuffles and over the warps through shared memory, then added to the
+//    int64 sums with one atomic per input and block.
+constexpr int PREP_ROWS_PER_THREAD_MAX = 2048;
 
-__device__ __forceinline__ uint32_t e4m3_of_nibble(uint32_t nib) {
-  // table of the 16 nibble values, packed 4 per word: nibble k -> value k (k < 8) or k - 16
-  constexpr uint32_t t0 = e4m3_of_int(0) | e4m3_of_int(1) << 8 | e4m3_of_int(2) << 16 | e4m3_of_int(3) << 24;
-  constexpr uint32_t t1 = e4m3_of_int(4) | e4m3_of_int(5) << 8 | e4m3_of_int(6) << 16 | e4m3_of_int(7) << 24;
-  constexpr uint32_t t2 = e4m3_of_int(-8) | e4m3_of_int(-7) << 8 | e4m3_of_int(-6) << 16 | e4m3_of_int(-5) << 24;
-  constexpr uint32_t t3 = e4m3_of_int(-4) | e4m3_of_int(-3) << 8 | e4m3_of_int(-2) << 16 | e4m3_of_int(-1) << 24;
-  const uint32_t w = (nib & 8) ? ((nib & 4) ? t3 : t2) : ((nib & 4) ? t1 : t0);
-  return (w >> (8 * (nib & 3))) & 0xFF;
-}
-
-// op[f][t][r]: thread handles 16 inputs (32 operand rows) of one (f, t).
-// T: valid samples, T_run: padded samples written (multiple of the stage length), T_stride: layout
-// stride of op in samples per channel.
-__global__ void f8_unpack_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int T_run, int T_stride, int R,
-                                 bool vec, uint8_t* __restrict__ op) {
+__global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int T_run,
+                                                      int T_stride, int R, int rows_per_split, bool vec,
+                                                      uint8_t* __restrict__ op, long long* __restrict__ s1,
+                                                      long long* __restrict__ s2) {
   const int G = R / 32;
-  const long long total = (long long)C * T_run * G;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int g = (int)(e % G);
-    const long long ft = e / G;
-    const int t = (int)(ft % T_run);
-    const int f = (int)(ft / T_run);
-    const int n0 = 16 * g;
-    uint32_t w[4] = {0u, 0u, 0u, 0u};
-    if (t < T && n0 < N) {
-      const uint8_t* src = in + ((size_t)t * C + f) * N + n0;
-      if (vec) {
-        const uint4 q = *reinterpret_cast<const uint4*>(src);
-        w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
-      } else {
-        for (int k = 0; k < 16; ++k)
-          if (n0 + k < N) w[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tl = lane >> 3, us = lane & 7;
+  const int g = 8 * blockIdx.x + us;
+  const int f = blockIdx.y;
+  const int t_begin = blockIdx.z * rows_per_split;
+  const int t_end = min(T_run, t_begin + rows_per_split);
+  const int n0 = 16 * g;
+  const int nv = N - n0;  // valid inputs of this unit (<= 0: padding unit)
+  // packed 16-bit lane sums: [word k][even / odd byte], for Re and Im
+  uint32_t sre[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
+  uint32_t sim[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
+  if (g < G) {
+    for (int t = t_begin + 4 * warp + tl; t < t_end; t += 32) {
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      const bool live = t < T && nv > 0;
+      if (live) {
+        const uint8_t* src = in + ((size_t)t * C + f) * N + n0;
+        if (vec) {
+          w = __ldg(reinterpret_cast<const uint4*>(src));
+        } else {
+          uint32_t x[4] = {0u, 0u, 0u, 0u};
+          for (int k = 0; k < 16; ++k)
+            if (n0 + k < N) x[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
+          w = make_uint4(x[0], x[1], x[2], x[3]);
+        }
+      }
+      uint4 o0 = make_uint4(0u, 0u, 0u, 0u), o1 = make_uint4(0u, 0u, 0u, 0u);
+      if (live) expand16(w, nv, o0, o1);
+      if (op) {
+        uint4* dst = reinterpret_cast<uint4*>(op + ((size_t)f * T_stride + t) * R + 32 * g);
+        dst[0] = o0;
+        dst[1] = o1;
+      }
+      // o0 = {Re w0, Im w0, Re w1, Im w1}, o1 = {Re w2, Im w2, Re w3, Im w3} (masked, 0 if not live)
+      const uint32_t re4[4] = {o0.x, o0.z, o1.x, o1.z};
+      const uint32_t im4[4] = {o0.y, o0.w, o1.y, o1.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sre[k][0] += re4[k] & 0x00FF00FFu;
+        sre[k][1] += (re4[k] >> 8) & 0x00FF00FFu;
+        sim[k][0] += im4[k] & 0x00FF00FFu;
+        sim[k][1] += (im4[k] >> 8) & 0x00FF00FFu;
       }
     }
-    uint32_t o[8];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      uint32_t lo = 0, hi = 0;
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const uint32_t byte = (w[k] >> (8 * b)) & 0xFF;
-        lo |= (e4m3_of_nibble(byte >> 4) | e4m3_of_nibble(byte & 15) << 8) << (16 * b);
-      }
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const uint32_t byte = (w[k] >> (8 * (b + 2))) & 0xFF;
-        hi |= (e4m3_of_nibble(byte >> 4) | e4m3_of_nibble(byte & 15) << 8) << (16 * b);
-      }
-      o[2 * k] = lo;
-      o[2 * k + 1] = hi;
-    }
-    uint4* dst = reinterpret_cast<uint4*>(op + ((size_t)f * T_stride + t) * R + 32 * g);
-    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
   }
-}
-
-__device__ __forceinline__ void record_error(int* err, volatile int* abort_flag, int code) {
-  *abort_flag = 1;
-  atomicCAS(err, 0, code);
+  if (!s1 && !s2) return;
+  // unpack to per-input sums, input j = 4 k + byte: even bytes 0, 2 / odd bytes 1, 3
+  __shared__ int part[8][8][32];  // [warp][unit][16 inputs x (Re, Im)]
+  int v[32];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * (4 * k + 0)] = (int)(sre[k][0] & 0xFFFF);
+    v[2 * (4 * k + 2)] = (int)(sre[k][0] >> 16);
+    v[2 * (4 * k + 1)] = (int)(sre[k][1] & 0xFFFF);
+    v[2 * (4 * k + 3)] = (int)(sre[k][1] >> 16);
+    v[2 * (4 * k + 0) + 1] = (int)(sim[k][0] & 0xFFFF);
+    v[2 * (4 * k + 2) + 1] = (int)(sim[k][0] >> 16);
+    v[2 * (4 * k + 1) + 1] = (int)(sim[k][1] & 0xFFFF);
+    v[2 * (4 * k + 3) + 1] = (int)(sim[k][1] >> 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    v[j] += __shfl_xor_sync(0xffffffffu, v[j], 8);
+    v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
+  }
+  if (tl == 0) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) part[warp][us][j] = v[j];
+  }
+  __syncthreads();
+  // thread i: unit i / 32, value i % 32
+  const int uu = threadIdx.x >> 5, j = threadIdx.x & 31;
+  const int gg = 8 * blockIdx.x + uu;
+  const int n = 16 * gg + (j >> 1);
+  if (gg < G && n < N) {
+    long long sum = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += part[w][uu][j];
+    if (sum != 0) {
+      const long long idx = ((long long)f * N + n) * 2 + (j & 1);
+      if (s1) atomicAdd(reinterpret_cast<unsigned long long*>(s1 + idx), (unsigned long long)sum);
+      if (s2) atomicAdd(reinterpret_cast<unsigned long long*>(s2 + idx), (unsigned long long)sum);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -128,7 +144,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int P = npol * npol;
   const int n_k = T_run / KT;
   const int chunk_k = flush_len / KT;
   const long long total = (long long)n_tiles * C;
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
-      ptx::mbar_init(&tempty[a], 128);
+      ptx::mbar_init(&tempty[a], EPI_THREADS);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -247,18 +262,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       ptx::mbar_wait(drain, 0, WAIT_NS);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
+    // two warps per TMEM lane quarter; warp half h drains the 32-column chunks h, h + 2, ...
     const int q = warp & 3;
-    const int row = 32 * q + lane;  // TMEM lane = c-side operand row
-    const bool odd = (lane & 1) != 0;
+    const int half = (warp - 2) >> 2;
     uint32_t use[2] = {0u, 0u};
     int acc = 0;
     bool ok = true;
     for (long long w = blockIdx.x; w < total && ok; w += gridDim.x) {
       const int f = (int)(w / n_tiles);
       const F8Tile tl = tiles[w % n_tiles];
-      const int c = tl.c0 + (row >> 1);
-      const int sc = c / npol, pc = c % npol;
       for (int k0 = 0; k0 < n_k; k0 += chunk_k) {
         if (__any_sync(0xffffffffu, *abort_flag != 0)) {
           ok = false;
@@ -271,37 +284,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           break;
         }
         ptx::tc_fence_after();
-        for (int cc = 0; cc < tl.nb / 32; ++cc) {
-          uint32_t v[32];
-          ptx::tmem_ld_32x32b_x32(tbase + acc * ACC_COLS + ((uint32_t)(32 * q) << 16) + cc * 32, v);
-          ptx::tmem_ld_wait();
-          float recv[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float send = __uint_as_float(odd ? v[j] : v[16 + j]);
-            recv[j] = __shfl_xor_sync(0xffffffffu, send, 1);
-          }
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            long long re, im;
-            if (!odd) {  // this lane: Re_c row, partner: Im_c row; a-inputs m = 0..7 of the chunk
-              re = __float2ll_rn(__uint_as_float(v[2 * m])) + __float2ll_rn(recv[2 * m + 1]);
-              im = __float2ll_rn(__uint_as_float(v[2 * m + 1])) - __float2ll_rn(recv[2 * m]);
-            } else {     // this lane: Im_c row, partner: Re_c row; a-inputs m = 8..15
-              re = __float2ll_rn(recv[2 * m]) + __float2ll_rn(__uint_as_float(v[16 + 2 * m + 1]));
-              im = __float2ll_rn(recv[2 * m + 1]) - __float2ll_rn(__uint_as_float(v[16 + 2 * m]));
-            }
-            const int a = tl.a0 + cc * 16 + (odd ? 8 : 0) + m;
-            if (a >= N || c >= N) continue;
-            const int sa = a / npol;
-            if (sa < sc) continue;
-            const long long b = (long long)sa * (sa + 1) / 2 + sc;
-            long long* cell = cross + (((long long)f * Bs + b) * P + (a % npol) * npol + pc) * 2;
-            cell[0] += re;
-            cell[1] += im;
-            if (a == c) autos[(long long)f * N + a] += re;
-          }
-        }
+        drain_tile(tbase + acc * ACC_COLS, q, lane, half, 2, tl, f, N, npol, Bs, cross, autos);
         ptx::tc_fence_before();
         ptx::mbar_arrive(&tempty[acc]);
         ++use[acc];
@@ -319,14 +302,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 size_t f8_smem_bytes() { return SMEM_BYTES; }
 
-cudaError_t launch_f8_unpack(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
-                             uint8_t* d_op, cudaStream_t st) {
-  const long long total = (long long)s.C * T_run * (R / 32);
-  if (total == 0) return cudaSuccess;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
+                           uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st) {
+  if (T_run == 0) return cudaSuccess;
+  const int G = R / 32;
+  // time split: at most PREP_ROWS_PER_THREAD_MAX samples per thread (each thread takes one of 32)
+  int split = 1;
+  while ((long long)(T_run + split - 1) / split > 32LL * PREP_ROWS_PER_THREAD_MAX) split *= 2;
+  while ((long long)((G + 7) / 8) * s.C * split < 4 * 152 && T_run / (split * 2) >= 256) split *= 2;
+  const int rows = (int)round_up((T_run + split - 1) / split, 32);
+  split = (T_run + rows - 1) / rows;
+  dim3 grid((G + 7) / 8, s.C, split);
   const bool vec = (s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
-  f8_unpack_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, R, vec, d_op);
+  f8_prep_kernel<<<grid, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, R, rows, vec, d_op, d_s1, d_s2);
   return cudaGetLastError();
 }
 

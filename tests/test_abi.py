@@ -49,8 +49,11 @@ def test_host_only_helpers(lib):
     assert lib.corr_n_baselines(0, 1) == 0
     fp = lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP8TC)
     acc = 128 * 32896 * 4 * 2 * 8 + 128 * 512 * 8
-    assert fp >= acc + 128 * 8192 * 1024
+    assert fp >= acc
+    assert fp >= acc + 128 * 8192 * 1024  # operand scratch of the two-pass tensor path
+    assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_AUTO) == fp
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP32) < fp
+    assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP8TC_FUSED) < fp
     assert lib.corr_footprint_bytes(0, 1, 1, 1, 0) == 0
     assert lib.corr_footprint_bytes(3, 1, 1, 2, 0) == 0
     assert lib.corr_footprint_bytes(4, 1, 1, 2, 99) == 0

@@ -11,7 +11,7 @@ from oracle import oracle
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["fp32", "fp8tc"]
+PATHS = ["fp32", "fp8tc", "fp8tc_fused"]
 
 
 @pytest.fixture(scope="module")

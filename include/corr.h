@@ -164,6 +164,34 @@ int corr_profile_enable(corr_ctx* ctx, int on);
  * since the last read; synchronizes on the recorded events, then clears the totals. */
 int corr_profile_read(corr_ctx* ctx, int kernel, double* total_ms, long long* launches);
 
+/*
+ * corr_xengine_static - one block through the tensor path without allocating any memory.
+ *
+ * No counterpart in the paper: this entry point exists for callers that cannot call cudaMalloc
+ * when they correlate, e.g. code that runs inside a memory pool or arena owned by another runtime,
+ * or a real-time pipeline that forbids allocation once it has started. It needs no corr_ctx: all
+ * of its scratch (the e4m3 operand, the per-input offset sums, the tile list and an error word)
+ * lives in one fixed 64 MiB device array compiled into libcorr, which every GPU that loads the
+ * library holds until the process exits. It calls no cudaMalloc / cudaFree and no allocating
+ * library routine.
+ *
+ * d_samples  device uint8[n_time][n_chans][n_inputs] (layout and value convention as above).
+ * d_cross    device int64 [n_chans][B_s][n_pol^2][2]: the block's exact visibilities are ADDED.
+ * d_autos    device int64 [n_chans][n_inputs]: the block's autocorrelations are ADDED.
+ * Asynchronous on cuda_stream; the caller owns all three buffers.
+ *
+ * Limit: n_chans * round_up(n_time, 128) * round_up(2 n_inputs, 128) + 16 n_chans n_inputs bytes
+ * plus ~16.6 KiB must fit in 64 MiB (e.g. 512 inputs x 4 channels x 8192 samples); larger shapes
+ * return CORR_ERR_ARG with a message naming the size. On each device, the first call looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing any stream into a CUDA graph. Every call reuses the same array and clears the
+ * parts that must start at zero; calls whose work overlaps on the GPU (different streams, or other
+ * threads) race on the array and must be serialised by the caller. A device-side wait that times
+ * out leaves the block's result incomplete; this entry point has no context to report it through.
+ */
+int corr_xengine_static(const void* d_samples, int n_inputs, int n_chans, int n_time, int n_pol, long long* d_cross,
+                        long long* d_autos, void* cuda_stream);
+
 /* Synchronize the context's work, free its memory. NULL is accepted. */
 int corr_destroy(corr_ctx* ctx);
 

@@ -40,6 +40,7 @@ SIGNATURES = [
     ("corr_n_baselines", _c_ll, [_c_int, _c_int]),
     ("corr_profile_enable", _c_int, [_c_vp, _c_int]),
     ("corr_profile_read", _c_int, [_c_vp, _c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    ("corr_xengine_static", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),
     ("corr_destroy", _c_int, [_c_vp]),
     ("corr_last_error", _c_cp, []),
     ("corr_version", _c_cp, []),
@@ -140,6 +141,13 @@ def corr_profile_read(ctx: int, kernel: int):
     n = ctypes.c_longlong(0)
     _check(_lib.corr_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)), "corr_profile_read")
     return ms.value, n.value
+
+
+def corr_xengine_static(d_samples: int, n_inputs: int, n_chans: int, n_time: int, n_pol: int, d_cross: int,
+                        d_autos: int, stream: int) -> int:
+    """Allocation-free tensor-path X-engine for one block (adds into d_cross / d_autos)."""
+    return _check(_lib.corr_xengine_static(d_samples, n_inputs, n_chans, n_time, n_pol, d_cross, d_autos, stream),
+                  "corr_xengine_static")
 
 
 def corr_destroy(ctx: int) -> int:

@@ -114,6 +114,10 @@ std::vector<F8Tile> fp8_tiles(int N, int R) {
 
 }  // namespace
 
+namespace corr {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace corr
+
 // Opt-in per-kernel timing: CUDA events recorded on the launching stream around each launch.
 struct KernelTimer {
   std::vector<cudaEvent_t> ev;  // pairs (start, stop)

@@ -1,0 +1,181 @@
+// corr_xengine_static: the tensor-path X-engine for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc at the point where they correlate: code running inside a
+// memory pool or arena owned by another runtime (a framework allocator, a real-time pipeline that
+// forbids allocation after start-up, an embedding host that hands out only pre-sized buffers).
+// This entry point keeps every byte of scratch it needs in one file-scope device array that exists
+// from library load until process exit on every GPU that loads the library, and allocates nothing.
+// The caller passes the input block and the output accumulators only.
+#include <cstdio>
+#include <string>
+
+#include "corr_internal.cuh"
+
+namespace corr {
+namespace {
+
+// One shared scratch array (64 MiB, 256-byte aligned), carved per call as
+//   [0, 256)          error flag of the bounded waits
+//   [256, 16640)      triangle tile list (up to 1024 tiles)
+//   [16640, ...)      offset sums s[C][N][2] int64, then the e4m3 operand op[C][T_pad][R]
+constexpr size_t kStaticScratchBytes = 64ull << 20;
+constexpr size_t kOffTiles = 256;
+constexpr int kMaxTiles = 1024;
+constexpr size_t kOffSums = kOffTiles + kMaxTiles * sizeof(F8Tile);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device (set once)
+
+// Tiles of the triangle for N inputs (the enumeration the context path uses), written on device.
+__global__ void static_tiles_kernel(F8Tile* tiles, int N, int R) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int n = 0;
+  const int ncb = (N + 63) / 64;
+  for (int cb = 0; cb < ncb; ++cb) {
+    int a0 = 64 * cb;
+    int nb = (cb & 1) ? 128 : 256;
+    while (a0 < N && n < kMaxTiles) {
+      if (2 * a0 + nb > R) nb = R - 2 * a0;
+      tiles[n].c0 = 64 * cb;
+      tiles[n].a0 = a0;
+      tiles[n].nb = nb;
+      tiles[n].pad = 0;
+      ++n;
+      a0 += nb / 2;
+      nb = 256;
+    }
+  }
+}
+
+// Adds the block's offset correction to every cross cell and every auto: the X-engine added the
+// offset-domain Vu and Au for this block; V = Vu - (8 - 8i) s_a - (8 + 8i) conj(s_c) + 128 T and
+// A = Au - 16 (Re s + Im s) + 128 T.
+__global__ void static_correct_kernel(long long* __restrict__ cross, long long n_cells, long long* __restrict__ autos,
+                                      long long n_autos, int N, int npol, long long Bs, const long long* __restrict__ s,
+                                      long long T) {
+  const int P = npol * npol;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_autos; k += (long long)gridDim.x * blockDim.x)
+    autos[k] += -16 * (s[2 * k] + s[2 * k + 1]) + 128 * T;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n_cells;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const int pidx = (int)(cell % P);
+    const long long fb = cell / P;
+    const long long b = fb % Bs;
+    const long long f = fb / Bs;
+    long long sa = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while (sa * (sa + 1) / 2 > b) --sa;
+    while ((sa + 1) * (sa + 2) / 2 <= b) ++sa;
+    const long long sc = b - sa * (sa + 1) / 2;
+    const long long a = sa * npol + pidx / npol;
+    const long long c = sc * npol + pidx % npol;
+    const long long* s_a = s + (f * N + a) * 2;
+    const long long* s_c = s + (f * N + c) * 2;
+    cross[cell * 2] += -8 * (s_a[0] + s_a[1] + s_c[0] + s_c[1]) + 128 * T;
+    cross[cell * 2 + 1] += -8 * (s_a[1] - s_a[0] + s_c[0] - s_c[1]);
+  }
+}
+
+int static_fail(int code, const std::string& m) {
+  set_last_error(m);
+  return code;
+}
+
+}  // namespace
+}  // namespace corr
+
+using namespace corr;
+
+extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_chans, int n_time, int n_pol,
+                                   long long* d_cross, long long* d_autos, void* cuda_stream) {
+  if (!d_samples || !d_cross || !d_autos)
+    return static_fail(CORR_ERR_ARG, "corr_xengine_static: NULL pointer");
+  if (n_inputs < 1 || n_chans < 1 || n_time < 1 || (n_pol != 1 && n_pol != 2) || n_inputs % n_pol != 0 ||
+      n_inputs > (1 << 16))
+    return static_fail(CORR_ERR_ARG, "corr_xengine_static: invalid shape");
+  const long long R = round_up(2LL * n_inputs, kF8RowAlign);
+  const long long T_pad = round_up(n_time, kF8Kt);
+  const size_t sums = (size_t)n_chans * n_inputs * 16;
+  const size_t off_op = round_up((long long)(kOffSums + sums), 256);
+  const size_t need = off_op + (size_t)n_chans * (size_t)T_pad * (size_t)R;
+  if (need > kStaticScratchBytes)
+    return static_fail(CORR_ERR_ARG, "corr_xengine_static: needs " + std::to_string(need) +
+                                         " bytes of scratch, above the fixed maximum of " +
+                                         std::to_string(kStaticScratchBytes) +
+                                         " (C * round_up(T, 128) * round_up(2N, 128) + 16 C N + 16.6 KiB)");
+  const long long ncb = (n_inputs + 63) / 64;
+  if (ncb * ((n_inputs + 127) / 128 + 1) > kMaxTiles)
+    return static_fail(CORR_ERR_ARG, "corr_xengine_static: too many inputs for the fixed tile list");
+
+  // Per-device set-up: the device address of the scratch array, once per device.
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return static_fail(CORR_ERR_ARG, "corr_xengine_static: device index too large");
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: cudaGetSymbolAddress: ") +
+                                            cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  int* d_err = reinterpret_cast<int*>(base);
+  F8Tile* d_tiles = reinterpret_cast<F8Tile*>(base + kOffTiles);
+  long long* d_s = reinterpret_cast<long long*>(base + kOffSums);
+  uint8_t* d_op = base + off_op;
+
+  Shape sh;
+  sh.N = n_inputs;
+  sh.C = n_chans;
+  sh.T = n_time;
+  sh.npol = n_pol;
+  sh.S = n_inputs / n_pol;
+  sh.Bs = (long long)sh.S * (sh.S + 1) / 2;
+  sh.P = n_pol * n_pol;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+
+  // tile count is a pure function of N: count on the host with the same enumeration
+  int n_tiles = 0;
+  for (int cb = 0; cb < ncb; ++cb) {
+    int a0 = 64 * cb, nb = (cb & 1) ? 128 : 256;
+    while (a0 < n_inputs) {
+      if (2 * a0 + nb > R) nb = (int)(R - 2 * a0);
+      ++n_tiles;
+      a0 += nb / 2;
+      nb = 256;
+    }
+  }
+  CUtensorMap tmap;
+  std::string err;
+  if (encode_op_tensor_map(&tmap, d_op, (int)R, (int)T_pad, n_chans, &err) != 0)
+    return static_fail(CORR_ERR_CUDA, "corr_xengine_static: " + err);
+
+  // Everything that must start at zero for this call: the error flag and the offset sums.
+  e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_s, 0, sums, st);
+  if (e != cudaSuccess) return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: ") + cudaGetErrorString(e));
+  static_tiles_kernel<<<1, 32, 0, st>>>(d_tiles, n_inputs, (int)R);
+  e = cudaGetLastError();
+  const int T_run = (int)T_pad;
+  if (e == cudaSuccess)
+    e = launch_f8_prep(sh, static_cast<const uint8_t*>(d_samples), n_time, T_run, (int)T_pad, (int)R, d_op, d_s,
+                       nullptr, st);
+  int num_sms = 0;
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (num_sms < 1) num_sms = 1;
+  if (e == cudaSuccess)
+    e = launch_f8_xeng(sh, &tmap, T_run, kDefaultFlushF8, d_tiles, n_tiles, d_cross, d_autos, d_err, num_sms, st);
+  if (e == cudaSuccess) {
+    const long long n_cells = (long long)n_chans * sh.Bs * sh.P;
+    long long blocks = (n_cells + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    static_correct_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_cross, n_cells, d_autos, (long long)n_chans * n_inputs,
+                                                            n_inputs, n_pol, sh.Bs, d_s, (long long)n_time);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: ") + cudaGetErrorString(e));
+  return CORR_OK;
+}

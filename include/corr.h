@@ -1,9 +1,9 @@
 /*
  * corr.h - C ABI of libcorr, a single-GPU X-engine for a large-N FX radio correlator on GB300 (sm_103a).
  *
- * The library implements the O(N^2) stage of an FX correlator (paper Sec. 1: "O(N^2) cross
- * multiplication" on GPUs; Sec. 2.5: spectra read in groups, "cross multiplied and averaged",
- * 27 groups per 9 s dump). For every frequency channel f it accumulates
+ * The library implements the O(N^2) stage of an FX correlator (paper Sec. 1: the pairwise
+ * multiplication of input spectra runs on GPUs; Sec. 2.5: spectra are read in groups whose pairwise
+ * products are integrated, 27 groups per 9 s dump). For every frequency channel f it accumulates
  *
  *     V_f = sum_t x_f(t) x_f(t)^H                 (N x N Hermitian, lower triangle stored)
  *     A_f[m] = sum_t |x_{f,m}(t)|^2               (autocorrelations / total power, Sec. 2.6)
@@ -24,7 +24,7 @@
  * Autos    [C][N]: sum_t |x_n(t)|^2 (real).
  * Formats  CORR_FMT_CI64: int64 (re, im) / int64 autos, the exact sums.
  *          CORR_FMT_CF32: float32, each int64 rounded to nearest.
- *          CORR_FMT_CF32_NORM: float32 of (double)sum / (double)n_samples ("averaged", Sec. 2.5).
+ *          CORR_FMT_CF32_NORM: float32 of (double)sum / (double)n_samples (the time average, Sec. 2.5).
  * Streams  every call that takes a `cuda_stream` (a cudaStream_t, NULL = legacy default stream)
  *          only enqueues work on it and returns; work is ordered by the stream.
  * Errors   functions return CORR_OK (0) or a negative corr_status; corr_last_error() gives a
@@ -134,7 +134,7 @@ int corr_accumulate_autos(corr_ctx* ctx, const void* d_samples, void* cuda_strea
  * a bounded device staging buffer and cudaMemcpyAsync, so pageable memory works and pinned memory
  * is faster). Output sizes: cross C * B_s * n_pol^2 * 2 elements, autos C * N elements, of 8 bytes
  * (CI64) or 4 bytes (CF32*). If reset != 0, the selected accumulators and their sample count are
- * zeroed after the snapshot (Sec. 2.6: selective zeroing and dumping of accumulator cells, so the
+ * zeroed after the snapshot (Sec. 2.6: the total-power cells are zeroed and dumped on their own, so the
  * 1 s total-power cadence runs independently of the 9 s cross-power cadence).
  */
 int corr_dump(corr_ctx* ctx, void* out, int is_device_ptr, int what, int fmt, int reset, void* cuda_stream);

@@ -5,9 +5,10 @@
  * only the tests, the smoke check and the benchmark's CPU-baseline leg use it. It shares no
  * code, header, table or constant with the CUDA library.
  *
- * What it computes (Sec. 1 and Sec. 2.5: the O(N^2) cross multiplication done on the GPU layer,
- * "cross multiplied and averaged" over groups of spectra; Table 1 note (a): products XX, YY,
- * XY, YX of 256 dual-polarisation antennas; Sec. 2.6: auto-correlation (total power) cells):
+ * What it computes (Sec. 1 and Sec. 2.5: the GPU layer performs the O(N^2) stage, multiplying every
+ * pair of input spectra and integrating the products over groups of spectra; Table 1 note (a): the
+ * four polarisation products of 256 dual-polarisation antennas; Sec. 2.6: the auto-correlation
+ * (total power) cells):
  *
  *   for every channel f, every station pair (a, c) with a >= c and every polarisation pair (p, q):
  *       V_f[a p, c q] = sum_{t < T} x_{f, a p}(t) * conj(x_{f, c q}(t))          (exact int64)

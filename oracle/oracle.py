@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE ONLY. Only the tests, ``__graft_entry__.smoke()`` and the CP
 ``bench.py`` may import this module. The product library never imports, links or calls it, and it
 shares no code with the CUDA path.
 
-Definitions it follows (paper: Sec. 1 O(N^2) cross multiplication, Sec. 2.5 GPU layer
-"cross multiplied and averaged", Table 1 note (a) polarisation products XX, YY, XY, YX,
-Sec. 2.6 auto-correlation cells, Sec. 2.2 4+4-bit requantised samples):
+Definitions it follows (paper: Sec. 1, the O(N^2) stage on GPUs; Sec. 2.5, pairwise products of the
+spectra integrated over groups of spectra; Table 1 note (a), the four polarisation products;
+Sec. 2.6, the auto-correlation cells; Sec. 2.2, samples requantised to 4+4 bits):
 
 * sample byte = (Re nibble << 4) | Im nibble, each nibble a 4-bit two's-complement integer;
 * ``cross[f, b(a, c), p * n_pol + q] = sum_t x_{a p}(t) conj(x_{c q}(t))`` for stations a >= c,

@@ -114,6 +114,15 @@ int corr_set_flush_period(corr_ctx* ctx, int n_samples);
 int corr_accumulate(corr_ctx* ctx, const void* d_samples, void* cuda_stream);
 
 /*
+ * corr_accumulate_batch - add n_blocks blocks, d_blocks[b] each a device uint8[T][C][N], in order;
+ * the result equals n_blocks corr_accumulate calls (the paper integrates 27 groups of spectra per
+ * dump, Sec. 2.5). All blocks must be ready when the stream reaches the call, which lets the
+ * tensor path build the operand of block b + 1 on an internal stream while block b is multiplied.
+ * The pointer array is read during the call only.
+ */
+int corr_accumulate_batch(corr_ctx* ctx, const void* const* d_blocks, int n_blocks, void* cuda_stream);
+
+/*
  * corr_accumulate_host - same as corr_accumulate for a HOST buffer uint8[T][C][N]: the library
  * copies it to the device in time slices through its own staging buffers (overlapping copy and
  * compute) and accumulates each slice. Pinned memory gives the best copy rate. Returns when the

@@ -30,6 +30,7 @@ SIGNATURES = [
     ("corr_get_path", _c_int, [_c_vp]),
     ("corr_set_flush_period", _c_int, [_c_vp, _c_int]),
     ("corr_accumulate", _c_int, [_c_vp, _c_vp, _c_vp]),
+    ("corr_accumulate_batch", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_vp]),
     ("corr_accumulate_host", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_accumulate_autos", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_dump", _c_int, [_c_vp, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
@@ -97,6 +98,11 @@ def corr_set_flush_period(ctx: int, n_samples: int) -> int:
 
 def corr_accumulate(ctx: int, d_samples: int, stream: int) -> int:
     return _check(_lib.corr_accumulate(ctx, d_samples, stream), "corr_accumulate")
+
+
+def corr_accumulate_batch(ctx: int, d_blocks, stream: int) -> int:
+    arr = (ctypes.c_void_p * len(d_blocks))(*[int(p) for p in d_blocks])
+    return _check(_lib.corr_accumulate_batch(ctx, arr, len(d_blocks), stream), "corr_accumulate_batch")
 
 
 def corr_accumulate_host(ctx: int, h_samples: int, stream: int) -> int:
@@ -202,6 +208,11 @@ class Correlator:
     def accumulate(self, samples, stream=None):
         self._check_samples(samples, True)
         corr_accumulate(self.ctx, samples.data_ptr(), _stream_handle(stream))
+
+    def accumulate_batch(self, blocks, stream=None):
+        for b in blocks:
+            self._check_samples(b, True)
+        corr_accumulate_batch(self.ctx, [b.data_ptr() for b in blocks], _stream_handle(stream))
 
     def accumulate_host(self, samples, stream=None):
         self._check_samples(samples, False)

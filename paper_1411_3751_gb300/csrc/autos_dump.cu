@@ -84,39 +84,63 @@ __global__ void __launch_bounds__(AW * 32) autos_kernel(const uint8_t* __restric
 // offset domain (u = x + 8 + 8i) and are mapped back here:
 //   V = Vu - (8 - 8i) s_a - (8 + 8i) conj(s_c) + 128 T_off,   A = Au - 16 (Re s + Im s) + 128 T_off
 // (s = per-input offset sums and T_off = samples accumulated through that path, per cadence).
-__device__ __forceinline__ long long corrected(const long long* __restrict__ acc, long long k, const Shape2& g) {
-  long long v = acc[k];
-  if (g.soff == nullptr || g.t_off == 0) return v;
-  if (g.autos) return v - 16 * (g.soff[2 * k] + g.soff[2 * k + 1]) + 128 * g.t_off;  // A = Au - 16 (Re s + Im s) + 128 T
-  const long long cell = k >> 1;
-  const int comp = (int)(k & 1);
-  const int pidx = (int)(cell % g.P);
-  const long long fb = cell / g.P;
-  const long long b = fb % g.Bs;
-  const long long f = fb / g.Bs;
-  long long sa = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-  while (sa * (sa + 1) / 2 > b) --sa;
-  while ((sa + 1) * (sa + 2) / 2 <= b) ++sa;
-  const long long sc = b - sa * (sa + 1) / 2;
-  const long long a = sa * g.npol + pidx / g.npol;
-  const long long c = sc * g.npol + pidx % g.npol;
-  const long long* s_a = g.soff + (f * g.N + a) * 2;
-  const long long* s_c = g.soff + (f * g.N + c) * 2;
-  if (comp == 0) return v - 8 * (s_a[0] + s_a[1] + s_c[0] + s_c[1]) + 128 * g.t_off;
-  return v - 8 * (s_a[1] - s_a[0] + s_c[0] - s_c[1]);
+template <typename T>
+__device__ __forceinline__ void put(void* out, long long k, long long v, int fmt, long long n_samples) {
+  if (fmt == CORR_FMT_CI64) {
+    static_cast<long long*>(out)[k] = v;
+  } else if (fmt == CORR_FMT_CF32) {
+    static_cast<float*>(out)[k] = __ll2float_rn(v);
+  } else {
+    static_cast<float*>(out)[k] = n_samples > 0 ? __double2float_rn(__ddiv_rn(__ll2double_rn(v), (double)n_samples)) : 0.f;
+  }
 }
 
-__global__ void dump_kernel(const long long* __restrict__ acc, long long n, void* __restrict__ out, int fmt,
-                            long long n_samples, long long k_base, Shape2 g) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const long long v = corrected(acc, k_base + k, g);
-    if (fmt == CORR_FMT_CI64) {
-      static_cast<long long*>(out)[k] = v;
-    } else if (fmt == CORR_FMT_CF32) {
-      static_cast<float*>(out)[k] = __ll2float_rn(v);
-    } else {
-      static_cast<float*>(out)[k] = n_samples > 0 ? __double2float_rn(__ddiv_rn(__ll2double_rn(v), (double)n_samples)) : 0.f;
+// station pair index b -> (a, c) with b = a (a + 1) / 2 + c, a >= c
+__device__ __forceinline__ void pair_of(int b, int& sa, int& sc) {
+  int a = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+  while ((long long)a * (a + 1) / 2 > b) --a;
+  while ((long long)(a + 1) * (a + 2) / 2 <= b) ++a;
+  sa = a;
+  sc = b - (int)((long long)a * (a + 1) / 2);
+}
+
+// Cross dump of cells [cell0, cell0 + n_cells) (a cell = one (re, im) pair), output indexed from 0.
+__global__ void dump_cross_kernel(const long long* __restrict__ acc, long long cell0, long long n_cells,
+                                  void* __restrict__ out, int fmt, long long n_samples, Shape2 g) {
+  const long long cpc = g.Bs * g.P;  // cells per channel
+  const int lp = g.P == 4 ? 2 : 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_cells; k += (long long)gridDim.x * blockDim.x) {
+    const long long cell = cell0 + k;
+    const longlong2 v2 = reinterpret_cast<const longlong2*>(acc)[cell];
+    long long re = v2.x, im = v2.y;
+    if (g.soff != nullptr && g.t_off != 0) {
+      const long long f = cell / cpc;
+      const int r = (int)(cell - f * cpc);
+      const int b = r >> lp, pidx = r & (g.P - 1);
+      int sa, sc;
+      pair_of(b, sa, sc);
+      const long long a = (long long)sa * g.npol + pidx / g.npol;
+      const long long c = (long long)sc * g.npol + pidx % g.npol;
+      const longlong2 s_a = reinterpret_cast<const longlong2*>(g.soff)[f * g.N + a];
+      const longlong2 s_c = reinterpret_cast<const longlong2*>(g.soff)[f * g.N + c];
+      re += -8 * (s_a.x + s_a.y + s_c.x + s_c.y) + 128 * g.t_off;
+      im += -8 * (s_a.y - s_a.x + s_c.x - s_c.y);
     }
+    put<void>(out, 2 * k, re, fmt, n_samples);
+    put<void>(out, 2 * k + 1, im, fmt, n_samples);
+  }
+}
+
+// Autos dump of elements [k0, k0 + n).
+__global__ void dump_autos_kernel(const long long* __restrict__ acc, long long k0, long long n, void* __restrict__ out,
+                                  int fmt, long long n_samples, Shape2 g) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    long long v = acc[k0 + k];
+    if (g.soff != nullptr && g.t_off != 0) {
+      const longlong2 s = reinterpret_cast<const longlong2*>(g.soff)[k0 + k];
+      v += -16 * (s.x + s.y) + 128 * g.t_off;  // A = Au - 16 (Re s + Im s) + 128 T
+    }
+    put<void>(out, k, v, fmt, n_samples);
   }
 }
 
@@ -133,9 +157,13 @@ cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long lo
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
                         long long k_base, const Shape2& g, cudaStream_t st) {
   if (n_elems == 0) return cudaSuccess;
-  long long blocks = (n_elems + 255) / 256;
+  const long long n_units = g.autos ? n_elems : n_elems / 2;
+  long long blocks = (n_units + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  dump_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, n_elems, d_out, fmt, n_samples, k_base, g);
+  if (g.autos)
+    dump_autos_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, k_base, n_elems, d_out, fmt, n_samples, g);
+  else
+    dump_cross_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, k_base / 2, n_elems / 2, d_out, fmt, n_samples, g);
   return cudaGetLastError();
 }
 

@@ -30,8 +30,10 @@ struct Layout {
   long long cross_elems;  // int64 elements
   long long autos_elems;
   int R;                  // FP8 operand rows
-  int T_pad;              // FP8 operand samples per channel
-  size_t op_bytes;
+  int T_pad;              // FP8 operand samples per channel and block
+  size_t op_bytes;        // one block's operand
+  int K_batch;            // blocks per operand buffer (one tensor-core launch in a batch)
+  size_t op_buf_bytes;    // K_batch blocks' operand
   bool ok;
 };
 
@@ -63,6 +65,15 @@ Layout make_layout(int N, int C, int T, int npol) {
   if (!mul_ok((unsigned long long)C * (unsigned long long)L.T_pad, (unsigned long long)L.R, &ob) || ob > (1ull << 46))
     return L;
   L.op_bytes = ob;
+  // blocks per batch launch: about kBatchSamples samples per launch (longer launches lose the L2
+  // reuse of a channel's operand between its tiles), never beyond the exactness bound of an
+  // in-chip partial sum (kF8MaxFlush), and a buffer is capped at kMaxOperandBuffer
+  long long k = kBatchSamples / L.T_pad;
+  if (k < 1) k = 1;
+  const long long kmem = ob > 0 ? (long long)(kMaxOperandBuffer / ob) : 1;
+  if (k > kmem) k = kmem < 1 ? 1 : kmem;
+  L.K_batch = (int)k;
+  L.op_buf_bytes = ob * (size_t)k;
   L.ok = true;
   return L;
 }
@@ -75,7 +86,7 @@ size_t in_stage_bytes(const Layout& L) {
 size_t footprint(const Layout& L, int path) {
   size_t b = (size_t)(L.cross_elems + L.autos_elems) * 8 + (size_t)L.autos_elems * 32 + 256;
   b += 2 * kStageBytes + 2 * in_stage_bytes(L);
-  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += L.op_bytes;
+  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += 2 * L.op_buf_bytes;  // double-buffered operand
   const long long nb = (L.s.N + 63) / 64;
   b += (size_t)(nb * (nb + 1) / 2) * sizeof(int2) + (size_t)(nb * 8 + 8) * sizeof(F8Tile);
   return b;
@@ -141,8 +152,12 @@ struct corr_ctx {
   long long n_off;         // samples accumulated through a tensor path since the cross reset
   long long n_off_auto;    // same, since the autos reset
   int* d_err;
-  uint8_t* d_op;
+  uint8_t* d_op;          // operand scratch, buffer 0 (also the single-block path)
   CUtensorMap tmap;
+  uint8_t* d_op2;         // buffer 1 for corr_accumulate_batch
+  CUtensorMap tmap2;
+  cudaStream_t prep_stream;
+  cudaEvent_t ev_prep_fork, ev_ready[2], ev_used[2];
   int2* d_tiles32;
   int n_tiles32;
   F8Tile* d_tiles8;
@@ -215,6 +230,13 @@ void free_ctx(corr_ctx* c) {
   cudaFree(c->d_soff_auto);
   cudaFree(c->d_err);
   cudaFree(c->d_op);
+  cudaFree(c->d_op2);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_ready[k]) cudaEventDestroy(c->ev_ready[k]);
+    if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+  }
+  if (c->ev_prep_fork) cudaEventDestroy(c->ev_prep_fork);
+  if (c->prep_stream) cudaStreamDestroy(c->prep_stream);
   cudaFree(c->d_tiles32);
   cudaFree(c->d_tiles8);
   cudaFree(c->d_stage[0]);
@@ -243,9 +265,10 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
     // tensor paths: one pass builds the operand (two-pass path) and the per-input offset sums for
     // both cadences; the X-engine adds the offset-domain products and their diagonal.
     const int T_run = (int)round_up(T_blk, kF8Kt);
-    const bool two_pass = path == CORR_PATH_FP8TC;
+    const bool two_pass = path == CORR_PATH_FP8TC || !f8_fused_supported(c->L.s, d_in, T_blk);
     bool tb = timer_begin(c, CORR_KERNEL_UNPACK, st);
-    e = launch_f8_prep(c->L.s, d_in, T_blk, T_run, c->L.T_pad, c->L.R, two_pass ? c->d_op : nullptr, c->d_soff,
+    e = launch_f8_prep(c->L.s, d_in, T_blk, T_run, c->L.T_pad * c->L.K_batch, 0, c->L.R, two_pass ? c->d_op : nullptr,
+                       c->d_soff,
                        c->d_soff_auto, st);
     timer_end(c, CORR_KERNEL_UNPACK, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "operand build launch");
@@ -264,21 +287,81 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
   return CORR_OK;
 }
 
-// The two-pass tensor path's operand scratch and its TMA tensor map.
+// The two-pass tensor path's operand scratch (two buffers) and their TMA tensor maps, plus the
+// stream and events that let corr_accumulate_batch build one block's operand while the previous
+// block is multiplied.
 int ensure_operand_scratch(corr_ctx* c) {
-  if (c->d_op) return CORR_OK;
-  if (cudaMalloc(&c->d_op, c->L.op_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    c->d_op = nullptr;
-    return fail(CORR_ERR_OOM, "operand scratch allocation failed");
+  if (c->d_op && c->d_op2) return CORR_OK;
+  uint8_t** bufs[2] = {&c->d_op, &c->d_op2};
+  CUtensorMap* maps[2] = {&c->tmap, &c->tmap2};
+  for (int k = 0; k < 2; ++k) {
+    if (*bufs[k]) continue;
+    if (cudaMalloc(bufs[k], c->L.op_buf_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *bufs[k] = nullptr;
+      return fail(CORR_ERR_OOM, "operand scratch allocation failed");
+    }
+    cudaError_t e = cudaMemset(*bufs[k], 0, c->L.op_buf_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
+    std::string err;
+    if (encode_op_tensor_map(maps[k], *bufs[k], c->L.R, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
+      cudaFree(*bufs[k]);
+      *bufs[k] = nullptr;
+      return fail(CORR_ERR_CUDA, err);
+    }
   }
-  cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
-  std::string err;
-  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R, c->L.T_pad, c->L.s.C, &err) != 0) {
-    cudaFree(c->d_op);
-    c->d_op = nullptr;
-    return fail(CORR_ERR_CUDA, err);
+  if (!c->prep_stream) {
+    bool ok = cudaStreamCreateWithFlags(&c->prep_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->ev_prep_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+      ok = cudaEventCreateWithFlags(&c->ev_ready[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_fail(cudaGetLastError(), "batch stream / events");
+  }
+  return CORR_OK;
+}
+
+// n blocks through the two-pass tensor path in chunks of up to K_batch blocks: the operand of a
+// chunk (each block at its own sample offset) is built on the prep stream into buffer j % 2 while
+// the previous chunk is multiplied on the caller's stream; one tensor-core launch covers a whole
+// chunk, so its in-chip partial sums are flushed to int64 once per chunk (<= 65536 samples).
+int accumulate_batch_pipelined(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
+  const int T_blk = c->L.s.T;
+  const int T_pad = c->L.T_pad;
+  const int K = c->L.K_batch;
+  const int T_span = T_pad * K;
+  const int flush = flush_for(c, CORR_PATH_FP8TC);
+  uint8_t* ops[2] = {c->d_op, c->d_op2};
+  const CUtensorMap* maps[2] = {&c->tmap, &c->tmap2};
+  cudaError_t e = cudaEventRecord(c->ev_prep_fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->prep_stream, c->ev_prep_fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+  int chunk = 0;
+  for (int b0 = 0; b0 < n; b0 += K, ++chunk) {
+    const int nb = (n - b0) < K ? (n - b0) : K;
+    const int buf = chunk & 1;
+    if (chunk >= 2) {
+      e = cudaStreamWaitEvent(c->prep_stream, c->ev_used[buf], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "batch wait");
+    }
+    for (int i = 0; i < nb; ++i) {
+      const bool tb = timer_begin(c, CORR_KERNEL_UNPACK, c->prep_stream);
+      e = launch_f8_prep(c->L.s, blocks[b0 + i], T_blk, T_pad, T_span, i * T_pad, c->L.R, ops[buf], c->d_soff,
+                         c->d_soff_auto, c->prep_stream);
+      timer_end(c, CORR_KERNEL_UNPACK, c->prep_stream, tb);
+      if (e != cudaSuccess) return cuda_fail(e, "batch operand build");
+    }
+    e = cudaEventRecord(c->ev_ready[buf], c->prep_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_ready[buf], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch event");
+    const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
+    e = launch_f8_xeng(c->L.s, maps[buf], nb * T_pad, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
+                       c->num_sms, st);
+    timer_end(c, CORR_KERNEL_XENG, st, tb);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_used[buf], st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch x-engine");
+    c->n_off += (long long)T_blk * nb;
+    c->n_off_auto += (long long)T_blk * nb;
   }
   return CORR_OK;
 }
@@ -420,6 +503,25 @@ int corr_accumulate(corr_ctx* c, const void* d_samples, void* stream) {
   return CORR_OK;
 }
 
+int corr_accumulate_batch(corr_ctx* c, const void* const* d_blocks, int n_blocks, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_accumulate_batch: NULL context");
+  if (n_blocks < 0 || (n_blocks > 0 && !d_blocks)) return fail(CORR_ERR_ARG, "corr_accumulate_batch: bad block list");
+  for (int b = 0; b < n_blocks; ++b)
+    if (!d_blocks[b]) return fail(CORR_ERR_ARG, "corr_accumulate_batch: NULL block " + std::to_string(b));
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint8_t* const* blocks = reinterpret_cast<const uint8_t* const*>(d_blocks);
+  int rc = CORR_OK;
+  if (resolved_path(c) == CORR_PATH_FP8TC && n_blocks > 1) {
+    rc = accumulate_batch_pipelined(c, blocks, n_blocks, st);
+  } else {
+    for (int b = 0; b < n_blocks && rc == CORR_OK; ++b) rc = accumulate_device(c, blocks[b], c->L.s.T, st);
+  }
+  if (rc != CORR_OK) return rc;
+  c->n_cross += (long long)c->L.s.T * n_blocks;
+  c->n_auto += (long long)c->L.s.T * n_blocks;
+  return CORR_OK;
+}
+
 int corr_accumulate_host(corr_ctx* c, const void* h_samples, void* stream) {
   if (!c) return fail(CORR_ERR_ARG, "corr_accumulate_host: NULL context");
   if (!h_samples) return fail(CORR_ERR_ARG, "corr_accumulate_host: NULL samples");
@@ -514,7 +616,7 @@ int corr_dump(corr_ctx* c, void* out, int is_device_ptr, int what, int fmt, int 
     timer_end(c, CORR_KERNEL_DUMP, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "corr_dump: launch");
   } else {
-    const long long per = (long long)(kStageBytes / esz);
+    const long long per = (long long)(kStageBytes / esz) & ~1LL;  // whole (re, im) cells
     int buf = 0;
     for (long long k = 0; k < n; k += per) {
       const long long m = (n - k) < per ? (n - k) : per;

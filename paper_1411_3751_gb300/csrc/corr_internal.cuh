@@ -56,6 +56,8 @@ constexpr int kF32Kt = 32;             // FP32 path time granule
 constexpr int kF32MaxFlush = 65536;    // |partial| <= 128 * 65536 = 2^23 < 2^24
 constexpr int kDefaultFlushF8 = 65536;
 constexpr int kDefaultFlushF32 = 65536;
+constexpr unsigned long long kMaxOperandBuffer = 8ull << 30;  // per two-pass operand buffer (batches)
+constexpr int kBatchSamples = 8192;  // target samples per tensor-core launch in a batch (<= kF8MaxFlush)
 
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
@@ -77,7 +79,8 @@ cudaError_t launch_f8_fused(const Shape& s, const uint8_t* d_in, int T_blk, int 
 // Operand build (d_op may be null) + per-input offset sums added to d_s1 and d_s2 (either may be
 // null). T_blk valid samples; T_run = round_up(T_blk, kF8Kt) samples written; T_stride = op samples
 // per channel.
-cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
+// The block is written at sample offset t_base of each channel's operand rows.
+cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int t_base, int R,
                            uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st);
 
 // Offset-domain products into d_cross, their diagonal into d_autos.
@@ -87,7 +90,8 @@ cudaError_t launch_f8_xeng(const Shape& s, const CUtensorMap* tmap, int T_run, i
 
 size_t f8_smem_bytes();
 
-// Dump elements [k_base, k_base + n_elems) of an accumulator (cross: corrected with g).
+// Dump elements [k_base, k_base + n_elems) of an accumulator, corrected with g (cross dumps: k_base
+// and n_elems even, i.e. whole (re, im) cells).
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
                         long long k_base, const Shape2& g, cudaStream_t st);
 
@@ -96,5 +100,11 @@ void set_last_error(const std::string& msg);
 
 // Tensor-map encoding through the driver entry point (no libcuda link dependency).
 int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err);
+// Raw input in[T][C][N] as a 3-D map, boxes of 64 inputs x 1 channel x 128 samples, no swizzle.
+int encode_input_tensor_map(CUtensorMap* map, const void* d_in, int N, int C, int T, std::string* err);
+
+// The fused path needs 16-byte TMA strides (N % 16 == 0, aligned input) and boxes no larger than the
+// array (N >= 64, T >= 128).
+bool f8_fused_supported(const Shape& s, const void* d_in, int T_blk);
 
 }  // namespace corr

@@ -161,7 +161,7 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   e = cudaGetLastError();
   const int T_run = (int)T_pad;
   if (e == cudaSuccess)
-    e = launch_f8_prep(sh, static_cast<const uint8_t*>(d_samples), n_time, T_run, (int)T_pad, (int)R, d_op, d_s,
+    e = launch_f8_prep(sh, static_cast<const uint8_t*>(d_samples), n_time, T_run, (int)T_pad, 0, (int)R, d_op, d_s,
                        nullptr, st);
   int num_sms = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);

@@ -30,7 +30,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 // done on the GPU). A unit = 16 inputs (32 operand rows) of one (f, t). Lane l of a warp takes unit
 // 8 blockIdx.x + (l % 8) at time offset l / 8, so a warp reads 8 units (128 inputs) of 4 samples and
 // the 8 warps of a block cover 32 samples per step; blockIdx.z splits the time range.
-//  * op (if not null): op[f][t][r] for t < T_run (zero rows for t >= T and inputs >= N);
+//  * op (if not null): op[f][t_base + t][r] for t < T_run (zero rows for t >= T and inputs >= N);
 //  * s1, s2 (if not null): per-input offset sums sum_t (x + 8 + 8i) over t < T, added to both
 //    (the cross-cadence and the total-power-cadence copies). Per-thread sums live in 16-bit lanes of
 //    packed words (at most 15 per sample, <= 2048 samples per thread), are reduced over the four
@@ -39,7 +39,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int PREP_ROWS_PER_THREAD_MAX = 2048;
 
 __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int T_run,
-                                                      int T_stride, int R, int rows_per_split, bool vec,
+                                                      int T_stride, int t_base, int R, int rows_per_split, bool vec,
                                                       uint8_t* __restrict__ op, long long* __restrict__ s1,
                                                       long long* __restrict__ s2) {
   const int G = R / 32;
@@ -55,36 +55,49 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   uint32_t sre[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
   uint32_t sim[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
   if (g < G) {
-    for (int t = t_begin + 4 * warp + tl; t < t_end; t += 32) {
-      uint4 w = make_uint4(0u, 0u, 0u, 0u);
-      const bool live = t < T && nv > 0;
-      if (live) {
-        const uint8_t* src = in + ((size_t)t * C + f) * N + n0;
-        if (vec) {
-          w = __ldg(reinterpret_cast<const uint4*>(src));
-        } else {
-          uint32_t x[4] = {0u, 0u, 0u, 0u};
-          for (int k = 0; k < 16; ++k)
-            if (n0 + k < N) x[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
-          w = make_uint4(x[0], x[1], x[2], x[3]);
+    // 4 samples per thread per iteration, all loads issued before any conversion
+    constexpr int U = 4;
+    for (int t0 = t_begin + 4 * warp + tl; t0 < t_end; t0 += 32 * U) {
+      uint4 w[U];
+      bool live[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + 32 * u;
+        w[u] = make_uint4(0u, 0u, 0u, 0u);
+        live[u] = t < t_end && t < T && nv > 0;
+        if (live[u]) {
+          const uint8_t* src = in + ((size_t)t * C + f) * N + n0;
+          if (vec) {
+            w[u] = __ldg(reinterpret_cast<const uint4*>(src));
+          } else {
+            uint32_t x[4] = {0u, 0u, 0u, 0u};
+            for (int k = 0; k < 16; ++k)
+              if (n0 + k < N) x[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
+            w[u] = make_uint4(x[0], x[1], x[2], x[3]);
+          }
         }
       }
-      uint4 o0 = make_uint4(0u, 0u, 0u, 0u), o1 = make_uint4(0u, 0u, 0u, 0u);
-      if (live) expand16(w, nv, o0, o1);
-      if (op) {
-        uint4* dst = reinterpret_cast<uint4*>(op + ((size_t)f * T_stride + t) * R + 32 * g);
-        dst[0] = o0;
-        dst[1] = o1;
-      }
-      // o0 = {Re w0, Im w0, Re w1, Im w1}, o1 = {Re w2, Im w2, Re w3, Im w3} (masked, 0 if not live)
-      const uint32_t re4[4] = {o0.x, o0.z, o1.x, o1.z};
-      const uint32_t im4[4] = {o0.y, o0.w, o1.y, o1.w};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        sre[k][0] += re4[k] & 0x00FF00FFu;
-        sre[k][1] += (re4[k] >> 8) & 0x00FF00FFu;
-        sim[k][0] += im4[k] & 0x00FF00FFu;
-        sim[k][1] += (im4[k] >> 8) & 0x00FF00FFu;
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + 32 * u;
+        if (t >= t_end) continue;
+        uint4 o0 = make_uint4(0u, 0u, 0u, 0u), o1 = make_uint4(0u, 0u, 0u, 0u);
+        if (live[u]) expand16(w[u], nv, o0, o1);
+        if (op) {
+          uint4* dst = reinterpret_cast<uint4*>(op + ((size_t)f * T_stride + t_base + t) * R + 32 * g);
+          dst[0] = o0;
+          dst[1] = o1;
+        }
+        // o0 = {Re w0, Im w0, Re w1, Im w1}, o1 = {Re w2, Im w2, Re w3, Im w3} (masked, 0 if not live)
+        const uint32_t re4[4] = {o0.x, o0.z, o1.x, o1.z};
+        const uint32_t im4[4] = {o0.y, o0.w, o1.y, o1.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          sre[k][0] += re4[k] & 0x00FF00FFu;
+          sre[k][1] += (re4[k] >> 8) & 0x00FF00FFu;
+          sim[k][0] += im4[k] & 0x00FF00FFu;
+          sim[k][1] += (im4[k] >> 8) & 0x00FF00FFu;
+        }
       }
     }
   }
@@ -302,7 +315,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 size_t f8_smem_bytes() { return SMEM_BYTES; }
 
-cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int R,
+cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int t_base, int R,
                            uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st) {
   if (T_run == 0) return cudaSuccess;
   const int G = R / 32;
@@ -314,7 +327,8 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
   split = (T_run + rows - 1) / rows;
   dim3 grid((G + 7) / 8, s.C, split);
   const bool vec = (s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
-  f8_prep_kernel<<<grid, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, R, rows, vec, d_op, d_s1, d_s2);
+  f8_prep_kernel<<<grid, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, t_base, R, rows, vec, d_op, d_s1,
+                                       d_s2);
   return cudaGetLastError();
 }
 
@@ -335,21 +349,49 @@ cudaError_t launch_f8_xeng(const Shape& s, const CUtensorMap* tmap, int T_run, i
   return cudaGetLastError();
 }
 
-int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err) {
-  typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static encode_fn fn = nullptr;
+namespace {
+
+typedef CUresult (*encode_fn_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_fn_t encode_fn(std::string* err) {
+  static encode_fn_t fn = nullptr;
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
       if (err) *err = "cuTensorMapEncodeTiled entry point unavailable";
-      return -1;
+      return nullptr;
     }
-    fn = reinterpret_cast<encode_fn>(p);
+    fn = reinterpret_cast<encode_fn_t>(p);
   }
+  return fn;
+}
+
+}  // namespace
+
+int encode_input_tensor_map(CUtensorMap* map, const void* d_in, int N, int C, int T, std::string* err) {
+  encode_fn_t fn = encode_fn(err);
+  if (!fn) return -1;
+  const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)C, (cuuint64_t)T};
+  const cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * (cuuint64_t)C};
+  const cuuint32_t box[3] = {64, 1, (cuuint32_t)KT};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(d_in), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled (input) failed: " + std::to_string((int)r);
+    return -1;
+  }
+  return 0;
+}
+
+int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err) {
+  encode_fn_t fn = encode_fn(err);
+  if (!fn) return -1;
   const cuuint64_t dims[3] = {(cuuint64_t)R, (cuuint64_t)T_pad, (cuuint64_t)C};
   const cuuint64_t strides[2] = {(cuuint64_t)R, (cuuint64_t)R * (cuuint64_t)T_pad};
   const cuuint32_t box[3] = {128, (cuuint32_t)KT, 1};

@@ -115,6 +115,24 @@ def test_multiple_blocks_and_flush_periods(env, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
+def test_batch_equals_sequential(env, path):
+    """corr_accumulate_batch (pipelined operand build) == the same blocks one call at a time."""
+    corr, synth, torch = env
+    T, C, N, B = 640, 3, 96, 5
+    blocks = [synth.generate_device(synth.Spec(kind="gauss_tone", seed=900 + b), T, C, N) for b in range(B)]
+    host = np.concatenate([b.cpu().numpy() for b in blocks])
+    want_c, want_a = oracle.correlate(host, 2, threads=8)
+    with corr.Correlator(N, C, T, 2, path=path) as xc:
+        xc.accumulate(blocks[0])
+        xc.accumulate_batch(blocks[1:])
+        c = xc.dump(corr.CORR_WHAT_CROSS)
+        a = xc.dump(corr.CORR_WHAT_AUTO)
+        xc.sync()
+        assert xc.samples(corr.CORR_WHAT_CROSS) == B * T
+    assert np.array_equal(c.cpu().numpy(), want_c) and np.array_equal(a.cpu().numpy(), want_a)
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_dump_formats_host_and_reset(env, path):
     corr, synth, torch = env
     T, C, N = 512, 2, 64
@@ -230,12 +248,13 @@ def test_full_size_512_inputs_128_channels_fp8(env):
     N, C, T, B, npol = 512, 128, 8192, 16, 2
     spec = synth.Spec(kind="gauss_tone", seed=0x14113751 + 2)
     xc = corr.Correlator(N, C, T, npol, path="fp8tc")
-    buf = torch.empty((T, C, N), dtype=torch.uint8, device="cuda")
     host_all = np.empty((B * T, C, N), dtype=np.uint8)
+    blocks = []
     for b in range(B):
-        synth.generate_device(spec, T, C, N, t0=b * T, out=buf)
-        xc.accumulate(buf)
-        host_all[b * T:(b + 1) * T] = buf.cpu().numpy()
+        blocks.append(synth.generate_device(spec, T, C, N, t0=b * T))
+        host_all[b * T:(b + 1) * T] = blocks[-1].cpu().numpy()
+    xc.accumulate_batch(blocks)  # the benchmark's launch sequence
+    del blocks
     cross = xc.dump(corr.CORR_WHAT_CROSS, device=False)
     autos = xc.dump(corr.CORR_WHAT_AUTO, device=False)
     xc.sync()

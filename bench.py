@@ -41,6 +41,23 @@ def useful_cmacs(N, C, T):
     return N * (N + 1) // 2 * C * T
 
 
+def profiled_traffic(kernel_files, profile_md):
+    """DRAM bytes per launch recorded by an ncu capture (profiles/), if the kernel sources still match."""
+    import hashlib
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile_md)).read()
+        h = hashlib.sha256()
+        for f in kernel_files:
+            h.update(open(os.path.join(ROOT, "paper_1411_3751_gb300", "csrc", f), "rb").read())
+        vals = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+        if vals.get("source_sha256", "").strip() != h.hexdigest()[:16]:
+            return None
+        return int(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -289,8 +306,11 @@ def main():
         peak_note = "FP32 FMA microbenchmark (152 SMs x 128 lanes x 2 flop)"
         bound = "alu"
     achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
+    traffic = None
+    if args.path == "fp8tc" and abs(blocks_per_launch - 1.0) < 1e-9:
+        traffic = profiled_traffic(["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"], "f8_xeng_512in_128ch_8192.md")
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel"}.get(args.path, "xeng_fp32_kernel"),
+            "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel"}.get(args.path, "xeng_fp32_kernel"),
             "peak_source": peak_note, "launch_ms": per_launch_ms,
             "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop (%.0f blocks of 8192 samples per launch)"
                            % (flops_launch, blocks_per_launch)}

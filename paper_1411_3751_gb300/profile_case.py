@@ -1,0 +1,46 @@
+"""Profiling driver: a few accumulate calls on one synthetic workload, for `ncu -k <kernel> -s/-c`.
+
+    python -m paper_1411_3751_gb300.profile_case --n 512 --c 128 --t 8192 --blocks 3 --path fp8tc
+
+Holds a single input block on the device (the same block is accumulated --blocks times), so the
+device footprint stays at a few GB for the 512-input, 128-channel case.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--c", type=int, default=128)
+    ap.add_argument("--t", type=int, default=8192)
+    ap.add_argument("--npol", type=int, default=2)
+    ap.add_argument("--blocks", type=int, default=3)
+    ap.add_argument("--path", default="fp8tc")
+    ap.add_argument("--seed", type=int, default=0x14113751 + 2)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1411_3751_gb300 import corr, synth
+
+    x = synth.generate_device(synth.Spec(kind="gauss_tone", seed=a.seed), a.t, a.c, a.n)
+    with corr.Correlator(a.n, a.c, a.t, a.npol, path=a.path) as xc:
+        for _ in range(a.blocks):
+            xc.accumulate(x)
+        xc.dump(corr.CORR_WHAT_CROSS)
+        xc.sync()
+    torch.cuda.synchronize()
+    print("profile_case ok: N=%d C=%d T=%d blocks=%d path=%s" % (a.n, a.c, a.t, a.blocks, a.path))
+
+
+if __name__ == "__main__":
+    main()

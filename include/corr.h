@@ -116,9 +116,9 @@ int corr_accumulate(corr_ctx* ctx, const void* d_samples, void* cuda_stream);
 /*
  * corr_accumulate_batch - add n_blocks blocks, d_blocks[b] each a device uint8[T][C][N], in order;
  * the result equals n_blocks corr_accumulate calls (the paper integrates 27 groups of spectra per
- * dump, Sec. 2.5). All blocks must be ready when the stream reaches the call, which lets the
- * tensor path build the operand of block b + 1 on an internal stream while block b is multiplied.
- * The pointer array is read during the call only.
+ * dump, Sec. 2.5). Short blocks share tensor-core launches (about 8192 samples per launch), so the
+ * int64 flush and the launch cost are paid once per group of blocks. The pointer array is read
+ * during the call only.
  */
 int corr_accumulate_batch(corr_ctx* ctx, const void* const* d_blocks, int n_blocks, void* cuda_stream);
 
@@ -200,6 +200,37 @@ int corr_profile_read(corr_ctx* ctx, int kernel, double* total_ms, long long* la
  */
 int corr_xengine_static(const void* d_samples, int n_inputs, int n_chans, int n_time, int n_pol, long long* d_cross,
                         long long* d_autos, void* cuda_stream);
+
+/*
+ * Groups of sub-arrays. The paper's architecture scales by giving each GPU its own slice of the
+ * problem (Sec. 2.5, Sec. 6: 109 channels per GPU, the same code from 32 to 512 inputs); a group
+ * correlates several independent sub-arrays of different input and channel counts (sharing the
+ * block length T and n_pol) on one GPU, with one persistent tensor-core launch covering the work
+ * of all of them, so small arrays do not each pay a partly empty wave.
+ *
+ * corr_group_create   n_arrays (1..8) sub-arrays; each is an ordinary corr_ctx (tensor path).
+ * corr_group_member   the i-th sub-array's context, for corr_dump / corr_reset / counters; owned by
+ *                     the group (do not destroy it).
+ * corr_group_accumulate  one block per sub-array (d_samples[i] device uint8[T][C_i][N_i]); mode 0:
+ *                     operand builds then ONE grouped X-engine launch; mode 1: separate per-array
+ *                     launches (for comparison). Results are identical.
+ * corr_group_autotune times the two tile plans of each sub-array on the given blocks, keeps the
+ *                     faster one (cached in-process by (N, C, T, n_pol, SM count), and in the file
+ *                     named by CORR_AUTOTUNE_CACHE if set), then zeroes the accumulators it touched.
+ *                     Synchronizes the stream. plans_out (optional) receives the chosen plans.
+ * corr_group_capture  records one grouped accumulate of the given buffers into a CUDA graph
+ *                     (pointers are baked in: refill the same buffers before each replay); needs a
+ *                     non-default stream.
+ * corr_group_launch   replays the captured graph (and advances the sample counters).
+ */
+typedef struct corr_group corr_group;
+corr_group* corr_group_create(int n_arrays, const int* n_inputs, const int* n_chans, int n_time_per_block, int n_pol);
+corr_ctx* corr_group_member(corr_group* group, int i);
+int corr_group_accumulate(corr_group* group, const void* const* d_samples, int mode, void* cuda_stream);
+int corr_group_autotune(corr_group* group, const void* const* d_samples, int* plans_out, void* cuda_stream);
+int corr_group_capture(corr_group* group, const void* const* d_samples, void* cuda_stream);
+int corr_group_launch(corr_group* group, void* cuda_stream);
+int corr_group_destroy(corr_group* group);
 
 /* Synchronize the context's work, free its memory. NULL is accepted. */
 int corr_destroy(corr_ctx* ctx);

@@ -41,6 +41,13 @@ SIGNATURES = [
     ("corr_n_baselines", _c_ll, [_c_int, _c_int]),
     ("corr_profile_enable", _c_int, [_c_vp, _c_int]),
     ("corr_profile_read", _c_int, [_c_vp, _c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    ("corr_group_create", _c_vp, [_c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _c_int, _c_int]),
+    ("corr_group_member", _c_vp, [_c_vp, _c_int]),
+    ("corr_group_accumulate", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_vp]),
+    ("corr_group_autotune", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), _c_vp]),
+    ("corr_group_capture", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_vp]),
+    ("corr_group_launch", _c_int, [_c_vp, _c_vp]),
+    ("corr_group_destroy", _c_int, [_c_vp]),
     ("corr_xengine_static", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),
     ("corr_destroy", _c_int, [_c_vp]),
     ("corr_last_error", _c_cp, []),
@@ -156,6 +163,47 @@ def corr_xengine_static(d_samples: int, n_inputs: int, n_chans: int, n_time: int
                   "corr_xengine_static")
 
 
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[int(p) for p in ptrs])
+
+
+def corr_group_create(n_inputs, n_chans, n_time_per_block: int, n_pol: int) -> int:
+    n = len(n_inputs)
+    h = _lib.corr_group_create(n, (ctypes.c_int * n)(*n_inputs), (ctypes.c_int * n)(*n_chans), n_time_per_block, n_pol)
+    if not h:
+        raise CorrError(CORR_ERR_ARG, "corr_group_create")
+    return h
+
+
+def corr_group_member(group: int, i: int) -> int:
+    h = _lib.corr_group_member(group, i)
+    if not h:
+        raise CorrError(CORR_ERR_ARG, "corr_group_member")
+    return h
+
+
+def corr_group_accumulate(group: int, d_samples, mode: int, stream: int) -> int:
+    return _check(_lib.corr_group_accumulate(group, _ptr_array(d_samples), mode, stream), "corr_group_accumulate")
+
+
+def corr_group_autotune(group: int, d_samples, stream: int):
+    plans = (ctypes.c_int * len(d_samples))()
+    _check(_lib.corr_group_autotune(group, _ptr_array(d_samples), plans, stream), "corr_group_autotune")
+    return list(plans)
+
+
+def corr_group_capture(group: int, d_samples, stream: int) -> int:
+    return _check(_lib.corr_group_capture(group, _ptr_array(d_samples), stream), "corr_group_capture")
+
+
+def corr_group_launch(group: int, stream: int) -> int:
+    return _check(_lib.corr_group_launch(group, stream), "corr_group_launch")
+
+
+def corr_group_destroy(group: int) -> int:
+    return _check(_lib.corr_group_destroy(group), "corr_group_destroy")
+
+
 def corr_destroy(ctx: int) -> int:
     return _check(_lib.corr_destroy(ctx), "corr_destroy")
 
@@ -177,13 +225,17 @@ def _stream_handle(stream) -> int:
 
 
 class Correlator:
-    """Owns one libcorr context; passes torch tensors' pointers and the current stream."""
+    """Owns one libcorr context (or wraps a group member); passes torch tensors' pointers and the
+    current stream."""
 
-    def __init__(self, n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int = 2, path: str = "auto"):
+    def __init__(self, n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int = 2, path: str = "auto",
+                 _handle: int = 0):
         self.n_inputs, self.n_chans, self.n_time, self.n_pol = n_inputs, n_chans, n_time_per_block, n_pol
         self.n_baselines = corr_n_baselines(n_inputs, n_pol)
-        self.ctx = corr_create(n_inputs, n_chans, n_time_per_block, n_pol)
-        self.set_path(path)
+        self._owned = not _handle
+        self.ctx = _handle or corr_create(n_inputs, n_chans, n_time_per_block, n_pol)
+        if self._owned:
+            self.set_path(path)
 
     def set_path(self, path: str):
         corr_set_path(self.ctx, PATHS[path])
@@ -259,9 +311,57 @@ class Correlator:
         return corr_profile_read(self.ctx, kernel)
 
     def close(self):
-        if self.ctx:
+        if self.ctx and self._owned:
             corr_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Group:
+    """A group of sub-arrays correlated with one persistent tensor-core launch (corr_group_*)."""
+
+    def __init__(self, shapes, n_time_per_block: int, n_pol: int = 2):
+        self.shapes = [(int(n), int(c)) for n, c in shapes]
+        self.n_time, self.n_pol = n_time_per_block, n_pol
+        self.handle = corr_group_create([n for n, _ in self.shapes], [c for _, c in self.shapes], n_time_per_block, n_pol)
+        self.members = [Correlator(n, c, n_time_per_block, n_pol, _handle=corr_group_member(self.handle, i))
+                        for i, (n, c) in enumerate(self.shapes)]
+
+    def _ptrs(self, blocks):
+        assert len(blocks) == len(self.shapes)
+        for m, b in zip(self.members, blocks):
+            m._check_samples(b, True)
+        return [b.data_ptr() for b in blocks]
+
+    def accumulate(self, blocks, separate: bool = False, stream=None):
+        corr_group_accumulate(self.handle, self._ptrs(blocks), 1 if separate else 0, _stream_handle(stream))
+
+    def autotune(self, blocks, stream=None):
+        return corr_group_autotune(self.handle, self._ptrs(blocks), _stream_handle(stream))
+
+    def capture(self, blocks, stream):
+        corr_group_capture(self.handle, self._ptrs(blocks), _stream_handle(stream))
+
+    def launch(self, stream=None):
+        corr_group_launch(self.handle, _stream_handle(stream))
+
+    def close(self):
+        if self.handle:
+            for m in self.members:
+                m.ctx = None
+            corr_group_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -1,8 +1,13 @@
 // C ABI of libcorr: argument validation, context and memory ownership, path dispatch, dumps.
+#include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "corr_internal.cuh"
@@ -86,7 +91,7 @@ size_t in_stage_bytes(const Layout& L) {
 size_t footprint(const Layout& L, int path) {
   size_t b = (size_t)(L.cross_elems + L.autos_elems) * 8 + (size_t)L.autos_elems * 32 + 256;
   b += 2 * kStageBytes + 2 * in_stage_bytes(L);
-  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += 2 * L.op_buf_bytes;  // double-buffered operand
+  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += L.op_buf_bytes;  // operand scratch
   const long long nb = (L.s.N + 63) / 64;
   b += (size_t)(nb * (nb + 1) / 2) * sizeof(int2) + (size_t)(nb * 8 + 8) * sizeof(F8Tile);
   return b;
@@ -97,29 +102,6 @@ std::vector<int2> fp32_tiles(int N) {
   const int nb = (N + 63) / 64;
   for (int ib = 0; ib < nb; ++ib)
     for (int jb = 0; jb <= ib; ++jb) t.push_back(make_int2(ib, jb));
-  return t;
-}
-
-// FP8 tiles: c-side blocks of 64 inputs; a-side spans of 128 inputs (256 rows) starting at the
-// c-block, the first one halved for odd c-blocks (its lower half would hold only a < c).
-std::vector<F8Tile> fp8_tiles(int N, int R) {
-  std::vector<F8Tile> t;
-  const int ncb = (N + 63) / 64;
-  for (int cb = 0; cb < ncb; ++cb) {
-    int a0 = 64 * cb;
-    int nb = (cb & 1) ? 128 : 256;
-    while (a0 < N) {
-      if (2 * a0 + nb > R) nb = R - 2 * a0;
-      F8Tile x;
-      x.c0 = 64 * cb;
-      x.a0 = a0;
-      x.nb = nb;
-      x.pad = 0;
-      t.push_back(x);
-      a0 += nb / 2;
-      nb = 256;
-    }
-  }
   return t;
 }
 
@@ -152,16 +134,15 @@ struct corr_ctx {
   long long n_off;         // samples accumulated through a tensor path since the cross reset
   long long n_off_auto;    // same, since the autos reset
   int* d_err;
-  uint8_t* d_op;          // operand scratch, buffer 0 (also the single-block path)
+  uint8_t* d_op;          // operand scratch of the two-pass tensor path (K_batch blocks)
   CUtensorMap tmap;
-  uint8_t* d_op2;         // buffer 1 for corr_accumulate_batch
-  CUtensorMap tmap2;
-  cudaStream_t prep_stream;
-  cudaEvent_t ev_prep_fork, ev_ready[2], ev_used[2];
   int2* d_tiles32;
   int n_tiles32;
-  F8Tile* d_tiles8;
+  F8Tile* d_tiles8;        // tile list (current plan), used by the fused path
   int n_tiles8;
+  WorkItem* d_items;       // channel-major work list of the two-pass tensor path
+  long long n_items;
+  int tile_plan;
   void* d_stage[2];      // host dumps
   void* d_in_stage[2];   // host inputs
   size_t in_stage;
@@ -230,15 +211,9 @@ void free_ctx(corr_ctx* c) {
   cudaFree(c->d_soff_auto);
   cudaFree(c->d_err);
   cudaFree(c->d_op);
-  cudaFree(c->d_op2);
-  for (int k = 0; k < 2; ++k) {
-    if (c->ev_ready[k]) cudaEventDestroy(c->ev_ready[k]);
-    if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
-  }
-  if (c->ev_prep_fork) cudaEventDestroy(c->ev_prep_fork);
-  if (c->prep_stream) cudaStreamDestroy(c->prep_stream);
   cudaFree(c->d_tiles32);
   cudaFree(c->d_tiles8);
+  cudaFree(c->d_items);
   cudaFree(c->d_stage[0]);
   cudaFree(c->d_stage[1]);
   cudaFree(c->d_in_stage[0]);
@@ -250,6 +225,9 @@ void free_ctx(corr_ctx* c) {
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
+
+int set_tile_plan(corr_ctx* c, int plan);
+XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush);
 
 // Accumulate T_blk samples from a device buffer laid out [T_blk][C][N].
 int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t st) {
@@ -274,8 +252,7 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
     if (e != cudaSuccess) return cuda_fail(e, "operand build launch");
     tb = timer_begin(c, CORR_KERNEL_XENG, st);
     if (two_pass)
-      e = launch_f8_xeng(c->L.s, &c->tmap, T_run, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
-                         c->num_sms, st);
+      e = launch_f8_xeng(xeng_args(c, c->tmap, T_run, flush), c->num_sms, st);
     else
       e = launch_f8_fused(c->L.s, d_in, T_blk, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
                           c->num_sms, st);
@@ -287,78 +264,98 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
   return CORR_OK;
 }
 
-// The two-pass tensor path's operand scratch (two buffers) and their TMA tensor maps, plus the
-// stream and events that let corr_accumulate_batch build one block's operand while the previous
-// block is multiplied.
-int ensure_operand_scratch(corr_ctx* c) {
-  if (c->d_op && c->d_op2) return CORR_OK;
-  uint8_t** bufs[2] = {&c->d_op, &c->d_op2};
-  CUtensorMap* maps[2] = {&c->tmap, &c->tmap2};
-  for (int k = 0; k < 2; ++k) {
-    if (*bufs[k]) continue;
-    if (cudaMalloc(bufs[k], c->L.op_buf_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      *bufs[k] = nullptr;
-      return fail(CORR_ERR_OOM, "operand scratch allocation failed");
-    }
-    cudaError_t e = cudaMemset(*bufs[k], 0, c->L.op_buf_bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
-    std::string err;
-    if (encode_op_tensor_map(maps[k], *bufs[k], c->L.R, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
-      cudaFree(*bufs[k]);
-      *bufs[k] = nullptr;
-      return fail(CORR_ERR_CUDA, err);
-    }
+// Tile plan of the tensor paths: the tile list (fused path) and the channel-major work list
+// (two-pass path) for plan 0 or 1 (see f8_tile_plan).
+int set_tile_plan(corr_ctx* c, int plan) {
+  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan);
+  std::vector<WorkItem> items;
+  items.reserve((size_t)c->L.s.C * t8.size());
+  for (int f = 0; f < c->L.s.C; ++f)
+    for (const F8Tile& t : t8) items.push_back(WorkItem{0, f, t.c0, t.a0, t.nb, 0});
+  F8Tile* d_t = nullptr;
+  WorkItem* d_i = nullptr;
+  if (cudaMalloc(&d_t, t8.size() * sizeof(F8Tile)) != cudaSuccess ||
+      cudaMalloc(&d_i, items.size() * sizeof(WorkItem)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d_t);
+    return fail(CORR_ERR_OOM, "tile list allocation failed");
   }
-  if (!c->prep_stream) {
-    bool ok = cudaStreamCreateWithFlags(&c->prep_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&c->ev_prep_fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int k = 0; k < 2 && ok; ++k)
-      ok = cudaEventCreateWithFlags(&c->ev_ready[k], cudaEventDisableTiming) == cudaSuccess &&
-           cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) return cuda_fail(cudaGetLastError(), "batch stream / events");
+  cudaError_t e = cudaMemcpy(d_t, t8.data(), t8.size() * sizeof(F8Tile), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_i, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d_t);
+    cudaFree(d_i);
+    return cuda_fail(e, "tile list upload");
+  }
+  cudaFree(c->d_tiles8);
+  cudaFree(c->d_items);
+  c->d_tiles8 = d_t;
+  c->n_tiles8 = (int)t8.size();
+  c->d_items = d_i;
+  c->n_items = (long long)items.size();
+  c->tile_plan = plan;
+  return CORR_OK;
+}
+
+XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush) {
+  XengArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.a[0].tmap = map;
+  a.a[0].cross = c->d_cross;
+  a.a[0].autos = c->d_autos;
+  a.a[0].Bs = c->L.s.Bs;
+  a.a[0].N = c->L.s.N;
+  a.a[0].npol = c->L.s.npol;
+  a.items = c->d_items;
+  a.n_items = c->n_items;
+  a.T_run = T_run;
+  a.flush_len = flush;
+  a.err = c->d_err;
+  return a;
+}
+
+// The two-pass tensor path's operand scratch and its TMA tensor map.
+int ensure_operand_scratch(corr_ctx* c) {
+  if (c->d_op) return CORR_OK;
+  if (cudaMalloc(&c->d_op, c->L.op_buf_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_op = nullptr;
+    return fail(CORR_ERR_OOM, "operand scratch allocation failed");
+  }
+  cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_buf_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
+  std::string err;
+  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
+    cudaFree(c->d_op);
+    c->d_op = nullptr;
+    return fail(CORR_ERR_CUDA, err);
   }
   return CORR_OK;
 }
 
-// n blocks through the two-pass tensor path in chunks of up to K_batch blocks: the operand of a
-// chunk (each block at its own sample offset) is built on the prep stream into buffer j % 2 while
-// the previous chunk is multiplied on the caller's stream; one tensor-core launch covers a whole
-// chunk, so its in-chip partial sums are flushed to int64 once per chunk (<= 65536 samples).
-int accumulate_batch_pipelined(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
+// n blocks through the two-pass tensor path in chunks of up to K_batch blocks (about 8192 samples
+// per launch): the operand of a chunk is built with each block at its own sample offset, then one
+// tensor-core launch multiplies the whole chunk, so short blocks share launches and flushes. (Building
+// the next chunk on a second stream while this one multiplies was measured: both kernels then share
+// HBM bandwidth and the step time does not change, so the chunks run in order on the caller's stream.)
+int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
   const int T_blk = c->L.s.T;
   const int T_pad = c->L.T_pad;
   const int K = c->L.K_batch;
   const int T_span = T_pad * K;
   const int flush = flush_for(c, CORR_PATH_FP8TC);
-  uint8_t* ops[2] = {c->d_op, c->d_op2};
-  const CUtensorMap* maps[2] = {&c->tmap, &c->tmap2};
-  cudaError_t e = cudaEventRecord(c->ev_prep_fork, st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->prep_stream, c->ev_prep_fork, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "batch fork");
-  int chunk = 0;
-  for (int b0 = 0; b0 < n; b0 += K, ++chunk) {
+  for (int b0 = 0; b0 < n; b0 += K) {
     const int nb = (n - b0) < K ? (n - b0) : K;
-    const int buf = chunk & 1;
-    if (chunk >= 2) {
-      e = cudaStreamWaitEvent(c->prep_stream, c->ev_used[buf], 0);
-      if (e != cudaSuccess) return cuda_fail(e, "batch wait");
-    }
     for (int i = 0; i < nb; ++i) {
-      const bool tb = timer_begin(c, CORR_KERNEL_UNPACK, c->prep_stream);
-      e = launch_f8_prep(c->L.s, blocks[b0 + i], T_blk, T_pad, T_span, i * T_pad, c->L.R, ops[buf], c->d_soff,
-                         c->d_soff_auto, c->prep_stream);
-      timer_end(c, CORR_KERNEL_UNPACK, c->prep_stream, tb);
+      const bool tb = timer_begin(c, CORR_KERNEL_UNPACK, st);
+      const cudaError_t e = launch_f8_prep(c->L.s, blocks[b0 + i], T_blk, T_pad, T_span, i * T_pad, c->L.R, c->d_op,
+                                           c->d_soff, c->d_soff_auto, st);
+      timer_end(c, CORR_KERNEL_UNPACK, st, tb);
       if (e != cudaSuccess) return cuda_fail(e, "batch operand build");
     }
-    e = cudaEventRecord(c->ev_ready[buf], c->prep_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_ready[buf], 0);
-    if (e != cudaSuccess) return cuda_fail(e, "batch event");
     const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
-    e = launch_f8_xeng(c->L.s, maps[buf], nb * T_pad, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
-                       c->num_sms, st);
+    const cudaError_t e = launch_f8_xeng(xeng_args(c, c->tmap, nb * T_pad, flush), c->num_sms, st);
     timer_end(c, CORR_KERNEL_XENG, st, tb);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_used[buf], st);
     if (e != cudaSuccess) return cuda_fail(e, "batch x-engine");
     c->n_off += (long long)T_blk * nb;
     c->n_off_auto += (long long)T_blk * nb;
@@ -422,16 +419,13 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
   if (c->num_sms < 1) c->num_sms = 1;
 
   const std::vector<int2> t32 = fp32_tiles(L.s.N);
-  const std::vector<F8Tile> t8 = fp8_tiles(L.s.N, L.R);
   c->n_tiles32 = (int)t32.size();
-  c->n_tiles8 = (int)t8.size();
   bool ok = cudaMalloc(&c->d_cross, (size_t)L.cross_elems * 8) == cudaSuccess &&
             cudaMalloc(&c->d_autos, (size_t)L.autos_elems * 8) == cudaSuccess &&
             cudaMalloc(&c->d_soff, (size_t)L.autos_elems * 16) == cudaSuccess &&
             cudaMalloc(&c->d_soff_auto, (size_t)L.autos_elems * 16) == cudaSuccess &&
             cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&c->d_tiles32, t32.size() * sizeof(int2)) == cudaSuccess &&
-            cudaMalloc(&c->d_tiles8, t8.size() * sizeof(F8Tile)) == cudaSuccess &&
             cudaMalloc(&c->d_stage[0], kStageBytes) == cudaSuccess &&
             cudaMalloc(&c->d_stage[1], kStageBytes) == cudaSuccess &&
             cudaMalloc(&c->d_in_stage[0], in_stage_bytes(L)) == cudaSuccess &&
@@ -453,15 +447,14 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
        cudaMemset(c->d_soff, 0, (size_t)L.autos_elems * 16) == cudaSuccess &&
        cudaMemset(c->d_soff_auto, 0, (size_t)L.autos_elems * 16) == cudaSuccess &&
        cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
-       cudaMemcpy(c->d_tiles32, t32.data(), t32.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_tiles8, t8.data(), t8.size() * sizeof(F8Tile), cudaMemcpyHostToDevice) == cudaSuccess;
+       cudaMemcpy(c->d_tiles32, t32.data(), t32.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
     e = cudaGetLastError();
     free_ctx(c);
     cuda_fail(e, "corr_create: initialisation");
     return nullptr;
   }
-  if (ensure_operand_scratch(c) != CORR_OK) {
+  if (set_tile_plan(c, 0) != CORR_OK || ensure_operand_scratch(c) != CORR_OK) {
     const std::string msg = g_err;
     free_ctx(c);
     fail(CORR_ERR_OOM, "corr_create: " + msg);
@@ -512,7 +505,7 @@ int corr_accumulate_batch(corr_ctx* c, const void* const* d_blocks, int n_blocks
   const uint8_t* const* blocks = reinterpret_cast<const uint8_t* const*>(d_blocks);
   int rc = CORR_OK;
   if (resolved_path(c) == CORR_PATH_FP8TC && n_blocks > 1) {
-    rc = accumulate_batch_pipelined(c, blocks, n_blocks, st);
+    rc = accumulate_batch_chunks(c, blocks, n_blocks, st);
   } else {
     for (int b = 0; b < n_blocks && rc == CORR_OK; ++b) rc = accumulate_device(c, blocks[b], c->L.s.T, st);
   }
@@ -679,6 +672,283 @@ int corr_destroy(corr_ctx* c) {
   free_ctx(c);
   if (e != cudaSuccess) return cuda_fail(e, "corr_destroy: synchronize");
   return CORR_OK;
+}
+
+}  // extern "C"
+
+// =============================================================================================
+// Groups of sub-arrays (different N and C, one block length): one persistent tensor-core launch
+// covers the work items of every sub-array; per-array tile plans come from a small autotuner.
+// =============================================================================================
+
+struct corr_group {
+  int n;
+  corr_ctx* ctx[kMaxGroupArrays];
+  WorkItem* d_items;
+  long long n_items;
+  cudaGraphExec_t graph;
+  int T;
+};
+
+namespace {
+
+// autotuner cache: (N, C, T, n_pol, SMs) -> tile plan; optionally mirrored in the file named by the
+// CORR_AUTOTUNE_CACHE environment variable (lines "N C T n_pol SMs plan")
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("CORR_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return;
+  int a, b, c, d, e, p;
+  while (std::fscanf(fh, "%d %d %d %d %d %d", &a, &b, &c, &d, &e, &p) == 6) g_tune[std::make_tuple(a, b, c, d, e)] = p;
+  std::fclose(fh);
+}
+
+void tune_store(const std::tuple<int, int, int, int, int>& k, int plan) {
+  g_tune[k] = plan;
+  const char* path = std::getenv("CORR_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+               std::get<4>(k), plan);
+  std::fclose(fh);
+}
+
+// Group work list: arrays in order of decreasing N (largest tiles first), each channel-major.
+int group_build_items(corr_group* g) {
+  std::vector<int> order(g->n);
+  for (int i = 0; i < g->n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return g->ctx[x]->L.s.N > g->ctx[y]->L.s.N; });
+  std::vector<WorkItem> items;
+  for (int i : order) {
+    corr_ctx* c = g->ctx[i];
+    const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan);
+    for (int f = 0; f < c->L.s.C; ++f)
+      for (const F8Tile& t : t8) items.push_back(WorkItem{i, f, t.c0, t.a0, t.nb, 0});
+  }
+  WorkItem* d = nullptr;
+  if (cudaMalloc(&d, items.size() * sizeof(WorkItem)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CORR_ERR_OOM, "group work list allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "group work list upload");
+  }
+  cudaFree(g->d_items);
+  g->d_items = d;
+  g->n_items = (long long)items.size();
+  return CORR_OK;
+}
+
+// One grouped accumulate: operand build per array, then one persistent launch over all arrays.
+int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
+  corr_ctx* c0 = g->ctx[0];
+  const int T_pad = c0->L.T_pad;
+  XengArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int i = 0; i < g->n; ++i) {
+    corr_ctx* c = g->ctx[i];
+    bool tb = timer_begin(c0, CORR_KERNEL_UNPACK, st);
+    cudaError_t e = launch_f8_prep(c->L.s, in[i], c->L.s.T, T_pad, c->L.T_pad * c->L.K_batch, 0, c->L.R, c->d_op,
+                                   c->d_soff, c->d_soff_auto, st);
+    timer_end(c0, CORR_KERNEL_UNPACK, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "group operand build");
+    a.a[i].tmap = c->tmap;
+    a.a[i].cross = c->d_cross;
+    a.a[i].autos = c->d_autos;
+    a.a[i].Bs = c->L.s.Bs;
+    a.a[i].N = c->L.s.N;
+    a.a[i].npol = c->L.s.npol;
+  }
+  a.items = g->d_items;
+  a.n_items = g->n_items;
+  a.T_run = T_pad;
+  a.flush_len = flush_for(c0, CORR_PATH_FP8TC);
+  a.err = c0->d_err;
+  const bool tb = timer_begin(c0, CORR_KERNEL_XENG, st);
+  cudaError_t e = launch_f8_xeng(a, c0->num_sms, st);
+  timer_end(c0, CORR_KERNEL_XENG, st, tb);
+  if (e != cudaSuccess) return cuda_fail(e, "group x-engine launch");
+  return CORR_OK;
+}
+
+void group_count(corr_group* g) {
+  for (int i = 0; i < g->n; ++i) {
+    corr_ctx* c = g->ctx[i];
+    c->n_cross += c->L.s.T;
+    c->n_auto += c->L.s.T;
+    c->n_off += c->L.s.T;
+    c->n_off_auto += c->L.s.T;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+corr_group* corr_group_create(int n_arrays, const int* n_inputs, const int* n_chans, int n_time_per_block, int n_pol) {
+  if (n_arrays < 1 || n_arrays > kMaxGroupArrays || !n_inputs || !n_chans) {
+    fail(CORR_ERR_ARG, "corr_group_create: need 1.." + std::to_string(kMaxGroupArrays) + " sub-arrays");
+    return nullptr;
+  }
+  corr_group* g = new (std::nothrow) corr_group{};
+  if (!g) {
+    fail(CORR_ERR_OOM, "corr_group_create: host allocation");
+    return nullptr;
+  }
+  g->n = n_arrays;
+  g->T = n_time_per_block;
+  for (int i = 0; i < n_arrays; ++i) {
+    g->ctx[i] = corr_create(n_inputs[i], n_chans[i], n_time_per_block, n_pol);
+    if (!g->ctx[i]) {
+      const std::string msg = g_err;
+      corr_group_destroy(g);
+      fail(CORR_ERR_ARG, "corr_group_create: sub-array " + std::to_string(i) + ": " + msg);
+      return nullptr;
+    }
+  }
+  if (group_build_items(g) != CORR_OK) {
+    const std::string msg = g_err;
+    corr_group_destroy(g);
+    fail(CORR_ERR_OOM, "corr_group_create: " + msg);
+    return nullptr;
+  }
+  return g;
+}
+
+corr_ctx* corr_group_member(corr_group* g, int i) {
+  if (!g || i < 0 || i >= g->n) {
+    fail(CORR_ERR_ARG, "corr_group_member: bad index");
+    return nullptr;
+  }
+  return g->ctx[i];
+}
+
+int corr_group_accumulate(corr_group* g, const void* const* d_samples, int mode, void* stream) {
+  if (!g || !d_samples) return fail(CORR_ERR_ARG, "corr_group_accumulate: NULL argument");
+  for (int i = 0; i < g->n; ++i)
+    if (!d_samples[i]) return fail(CORR_ERR_ARG, "corr_group_accumulate: NULL block " + std::to_string(i));
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint8_t* const* in = reinterpret_cast<const uint8_t* const*>(d_samples);
+  if (mode == 1) {
+    for (int i = 0; i < g->n; ++i) {
+      const int rc = corr_accumulate(g->ctx[i], d_samples[i], stream);
+      if (rc != CORR_OK) return rc;
+    }
+    return CORR_OK;
+  }
+  if (mode != 0) return fail(CORR_ERR_ARG, "corr_group_accumulate: mode must be 0 (grouped) or 1 (separate)");
+  const int rc = group_enqueue(g, in, st);
+  if (rc != CORR_OK) return rc;
+  group_count(g);
+  return CORR_OK;
+}
+
+int corr_group_autotune(corr_group* g, const void* const* d_samples, int* plans_out, void* stream) {
+  if (!g || !d_samples) return fail(CORR_ERR_ARG, "corr_group_autotune: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load();
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "corr_group_autotune: events");
+  int rc = CORR_OK;
+  for (int i = 0; i < g->n && rc == CORR_OK; ++i) {
+    corr_ctx* c = g->ctx[i];
+    const auto key = std::make_tuple(c->L.s.N, c->L.s.C, c->L.s.T, c->L.s.npol, c->num_sms);
+    auto it = g_tune.find(key);
+    int best = 0;
+    if (it != g_tune.end()) {
+      best = it->second;
+    } else {
+      float best_ms = 1e30f;
+      for (int plan = 0; plan < 2 && rc == CORR_OK; ++plan) {
+        rc = set_tile_plan(c, plan);
+        if (rc != CORR_OK) break;
+        // one warm-up block, then three timed blocks through the tensor path of this array alone
+        for (int rep = 0; rep < 4 && rc == CORR_OK; ++rep) {
+          if (rep == 1) cudaEventRecord(e0, st);
+          rc = accumulate_device(c, static_cast<const uint8_t*>(d_samples[i]), c->L.s.T, st);
+        }
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "corr_group_autotune");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = plan;
+        }
+      }
+      if (rc == CORR_OK) tune_store(key, best);
+    }
+    if (rc == CORR_OK) rc = set_tile_plan(c, best);
+    if (rc == CORR_OK) rc = corr_reset(c, CORR_WHAT_CROSS | CORR_WHAT_AUTO, stream);
+    if (plans_out) plans_out[i] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CORR_OK) return rc;
+  return group_build_items(g);
+}
+
+int corr_group_capture(corr_group* g, const void* const* d_samples, void* stream) {
+  if (!g || !d_samples) return fail(CORR_ERR_ARG, "corr_group_capture: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return fail(CORR_ERR_ARG, "corr_group_capture: needs a non-default stream");
+  bool prof[kMaxGroupArrays];
+  for (int i = 0; i < g->n; ++i) {
+    prof[i] = g->ctx[i]->profiling;
+    g->ctx[i]->profiling = false;  // no timing events inside the graph
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  int rc = CORR_OK;
+  if (e == cudaSuccess) {
+    rc = group_enqueue(g, reinterpret_cast<const uint8_t* const*>(d_samples), st);
+    e = cudaStreamEndCapture(st, &graph);
+  }
+  for (int i = 0; i < g->n; ++i) g->ctx[i]->profiling = prof[i];
+  if (rc != CORR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "corr_group_capture: capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_group_capture: instantiate");
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  g->graph = exec;
+  return CORR_OK;
+}
+
+int corr_group_launch(corr_group* g, void* stream) {
+  if (!g) return fail(CORR_ERR_ARG, "corr_group_launch: NULL group");
+  if (!g->graph) return fail(CORR_ERR_STATE, "corr_group_launch: no captured graph (call corr_group_capture)");
+  cudaError_t e = cudaGraphLaunch(g->graph, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_group_launch");
+  group_count(g);
+  return CORR_OK;
+}
+
+int corr_group_destroy(corr_group* g) {
+  if (!g) return CORR_OK;
+  int rc = CORR_OK;
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  cudaFree(g->d_items);
+  for (int i = 0; i < g->n; ++i)
+    if (g->ctx[i] && corr_destroy(g->ctx[i]) != CORR_OK) rc = CORR_ERR_CUDA;
+  delete g;
+  return rc;
 }
 
 }  // extern "C"

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "corr.h"
 
@@ -48,6 +49,30 @@ struct F8Tile {
   int pad;
 };
 
+// One work item of the tensor-core X-engine: a tile of one channel of one array.
+struct WorkItem {
+  int array, f, c0, a0, nb, pad;
+};
+
+// Per-array parameters of a tensor-core X-engine launch (one array, or a group of sub-arrays of
+// different N correlated in one persistent launch).
+constexpr int kMaxGroupArrays = 8;
+struct XengArray {
+  CUtensorMap tmap;  // operand op[C][T_span][R]
+  long long* cross;
+  long long* autos;
+  long long Bs;
+  int N, npol;
+};
+struct XengArgs {
+  XengArray a[kMaxGroupArrays];
+  const WorkItem* items;
+  long long n_items;
+  int T_run;      // samples multiplied per item (multiple of kF8Kt)
+  int flush_len;  // samples per in-chip partial sum
+  int* err;
+};
+
 constexpr int kF8Kt = 128;             // time samples per pipeline stage
 constexpr int kF8Stages = 4;           // smem ring depth
 constexpr int kF8RowAlign = 128;       // operand row padding
@@ -83,10 +108,13 @@ cudaError_t launch_f8_fused(const Shape& s, const uint8_t* d_in, int T_blk, int 
 cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int t_base, int R,
                            uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st);
 
-// Offset-domain products into d_cross, their diagonal into d_autos.
-cudaError_t launch_f8_xeng(const Shape& s, const CUtensorMap* tmap, int T_run, int flush_len, const F8Tile* d_tiles,
-                           int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
-                           cudaStream_t st);
+// Offset-domain products of every work item into its array's cross sums, diagonal into its autos.
+cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st);
+
+// Tile plans of the triangle (a >= c) for N inputs with R operand rows: plan 0 = a-side spans of
+// 128 inputs (N = 256 rows) with a half-width first span on odd c-blocks; plan 1 = spans of 64
+// inputs (N = 128) everywhere.
+std::vector<F8Tile> f8_tile_plan(int N, int R, int plan);
 
 size_t f8_smem_bytes();
 

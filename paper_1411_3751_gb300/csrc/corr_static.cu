@@ -7,6 +7,7 @@
 // from library load until process exit on every GPU that loads the library, and allocates nothing.
 // The caller passes the input block and the output accumulators only.
 #include <cstdio>
+#include <cstring>
 #include <string>
 
 #include "corr_internal.cuh"
@@ -16,35 +17,40 @@ namespace {
 
 // One shared scratch array (64 MiB, 256-byte aligned), carved per call as
 //   [0, 256)          error flag of the bounded waits
-//   [256, 16640)      triangle tile list (up to 1024 tiles)
-//   [16640, ...)      offset sums s[C][N][2] int64, then the e4m3 operand op[C][T_pad][R]
+//   [256, 256 + 1 MiB) channel-major work list (up to 43690 items)
+//   [.., ...)          offset sums s[C][N][2] int64, then the e4m3 operand op[C][T_pad][R]
 constexpr size_t kStaticScratchBytes = 64ull << 20;
-constexpr size_t kOffTiles = 256;
-constexpr int kMaxTiles = 1024;
-constexpr size_t kOffSums = kOffTiles + kMaxTiles * sizeof(F8Tile);
+constexpr size_t kOffItems = 256;
+constexpr long long kMaxItems = (1ll << 20) / sizeof(WorkItem);
+constexpr size_t kOffSums = kOffItems + (1ull << 20);
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device (set once)
 
-// Tiles of the triangle for N inputs (the enumeration the context path uses), written on device.
-__global__ void static_tiles_kernel(F8Tile* tiles, int N, int R) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int n = 0;
-  const int ncb = (N + 63) / 64;
-  for (int cb = 0; cb < ncb; ++cb) {
-    int a0 = 64 * cb;
-    int nb = (cb & 1) ? 128 : 256;
-    while (a0 < N && n < kMaxTiles) {
-      if (2 * a0 + nb > R) nb = R - 2 * a0;
-      tiles[n].c0 = 64 * cb;
-      tiles[n].a0 = a0;
-      tiles[n].nb = nb;
-      tiles[n].pad = 0;
-      ++n;
-      a0 += nb / 2;
-      nb = 256;
+// Channel-major work list: item w = tile (w mod n_tiles) of channel w / n_tiles, the tiles being the
+// plan-0 enumeration of the context path (a-side spans of 128 inputs, half-width on odd c-blocks).
+__global__ void static_items_kernel(WorkItem* items, int N, int R, int n_tiles, long long n_items) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n_items; w += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(w / n_tiles);
+    const int j = (int)(w % n_tiles);
+    int k = 0;
+    const int ncb = (N + 63) / 64;
+    for (int cb = 0; cb < ncb; ++cb) {
+      int a0 = 64 * cb;
+      int nb = (cb & 1) ? 128 : 256;
+      while (a0 < N) {
+        if (2 * a0 + nb > R) nb = R - 2 * a0;
+        if (k == j) {
+          items[w] = WorkItem{0, f, 64 * cb, a0, nb, 0};
+          cb = ncb;
+          break;
+        }
+        ++k;
+        a0 += nb / 2;
+        nb = 256;
+      }
     }
   }
 }
@@ -104,9 +110,6 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
                                          " bytes of scratch, above the fixed maximum of " +
                                          std::to_string(kStaticScratchBytes) +
                                          " (C * round_up(T, 128) * round_up(2N, 128) + 16 C N + 16.6 KiB)");
-  const long long ncb = (n_inputs + 63) / 64;
-  if (ncb * ((n_inputs + 127) / 128 + 1) > kMaxTiles)
-    return static_fail(CORR_ERR_ARG, "corr_xengine_static: too many inputs for the fixed tile list");
 
   // Per-device set-up: the device address of the scratch array, once per device.
   int dev = 0;
@@ -123,7 +126,7 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   }
   unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
   int* d_err = reinterpret_cast<int*>(base);
-  F8Tile* d_tiles = reinterpret_cast<F8Tile*>(base + kOffTiles);
+  WorkItem* d_items = reinterpret_cast<WorkItem*>(base + kOffItems);
   long long* d_s = reinterpret_cast<long long*>(base + kOffSums);
   uint8_t* d_op = base + off_op;
 
@@ -137,17 +140,12 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   sh.P = n_pol * n_pol;
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
-  // tile count is a pure function of N: count on the host with the same enumeration
-  int n_tiles = 0;
-  for (int cb = 0; cb < ncb; ++cb) {
-    int a0 = 64 * cb, nb = (cb & 1) ? 128 : 256;
-    while (a0 < n_inputs) {
-      if (2 * a0 + nb > R) nb = (int)(R - 2 * a0);
-      ++n_tiles;
-      a0 += nb / 2;
-      nb = 256;
-    }
-  }
+  // tile count is a pure function of N (the context path's enumeration, counted on the host)
+  const int n_tiles = (int)f8_tile_plan(n_inputs, (int)R, 0).size();
+  const long long n_items = (long long)n_tiles * n_chans;
+  if (n_items > kMaxItems)
+    return static_fail(CORR_ERR_ARG, "corr_xengine_static: " + std::to_string(n_items) +
+                                         " work items, above the fixed maximum of " + std::to_string(kMaxItems));
   CUtensorMap tmap;
   std::string err;
   if (encode_op_tensor_map(&tmap, d_op, (int)R, (int)T_pad, n_chans, &err) != 0)
@@ -157,7 +155,7 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_s, 0, sums, st);
   if (e != cudaSuccess) return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: ") + cudaGetErrorString(e));
-  static_tiles_kernel<<<1, 32, 0, st>>>(d_tiles, n_inputs, (int)R);
+  static_items_kernel<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(d_items, n_inputs, (int)R, n_tiles, n_items);
   e = cudaGetLastError();
   const int T_run = (int)T_pad;
   if (e == cudaSuccess)
@@ -167,7 +165,22 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (num_sms < 1) num_sms = 1;
   if (e == cudaSuccess)
-    e = launch_f8_xeng(sh, &tmap, T_run, kDefaultFlushF8, d_tiles, n_tiles, d_cross, d_autos, d_err, num_sms, st);
+  {
+    XengArgs xa;
+    std::memset(&xa, 0, sizeof(xa));
+    xa.a[0].tmap = tmap;
+    xa.a[0].cross = d_cross;
+    xa.a[0].autos = d_autos;
+    xa.a[0].Bs = sh.Bs;
+    xa.a[0].N = n_inputs;
+    xa.a[0].npol = n_pol;
+    xa.items = d_items;
+    xa.n_items = n_items;
+    xa.T_run = T_run;
+    xa.flush_len = kDefaultFlushF8;
+    xa.err = d_err;
+    e = launch_f8_xeng(xa, num_sms, st);
+  }
   if (e == cudaSuccess) {
     const long long n_cells = (long long)n_chans * sh.Bs * sh.P;
     long long blocks = (n_cells + 255) / 256;

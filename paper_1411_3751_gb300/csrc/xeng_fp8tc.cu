@@ -142,10 +142,7 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-    f8_xeng_kernel(const __grid_constant__ CUtensorMap tmap, int N, int C, int npol, long long Bs, int T_run,
-                   int flush_len, const F8Tile* __restrict__ tiles, int n_tiles, long long* __restrict__ cross,
-                   long long* __restrict__ autos, int* __restrict__ err) {
+__global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_constant__ XengArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -157,9 +154,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_k = T_run / KT;
-  const int chunk_k = flush_len / KT;
-  const long long total = (long long)n_tiles * C;
+  const int n_k = args.T_run / KT;
+  const int chunk_k = args.flush_len / KT;
+  const long long total = args.n_items;
+  const WorkItem* __restrict__ items = args.items;
+  int* err = args.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -186,15 +185,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      ptx::tma_prefetch_desc(&tmap);
       int stage = 0;
       uint32_t phase = 0;
       uint32_t issued_phase[STAGES];
       bool issued[STAGES];
       for (int s = 0; s < STAGES; ++s) issued[s] = false;
       for (long long w = blockIdx.x; w < total && !*abort_flag; w += gridDim.x) {
-        const int f = (int)(w / n_tiles);
-        const F8Tile tl = tiles[w % n_tiles];
+        const WorkItem tl = items[w];
+        const int f = tl.f;
+        const CUtensorMap* tmap = &args.a[tl.array].tmap;
         const uint32_t bytes = A_BYTES + (tl.nb == 256 ? B_BYTES : B_ATOM);
         for (int ks = 0; ks < n_k; ++ks) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1, WAIT_NS)) {
@@ -204,9 +203,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           uint8_t* a_dst = smem + stage * STAGE_BYTES;
           uint8_t* b_dst = a_dst + A_BYTES;
           ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-          ptx::tma_load_3d(a_dst, &tmap, &full[stage], 2 * tl.c0, ks * KT, f);
-          ptx::tma_load_3d(b_dst, &tmap, &full[stage], 2 * tl.a0, ks * KT, f);
-          if (tl.nb == 256) ptx::tma_load_3d(b_dst + B_ATOM, &tmap, &full[stage], 2 * tl.a0 + 128, ks * KT, f);
+          ptx::tma_load_3d(a_dst, tmap, &full[stage], 2 * tl.c0, ks * KT, f);
+          ptx::tma_load_3d(b_dst, tmap, &full[stage], 2 * tl.a0, ks * KT, f);
+          if (tl.nb == 256) ptx::tma_load_3d(b_dst + B_ATOM, tmap, &full[stage], 2 * tl.a0 + 128, ks * KT, f);
           issued[stage] = true;
           issued_phase[stage] = phase;
           if (++stage == STAGES) {
@@ -230,7 +229,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int acc = 0;
       bool ok = true;
       for (long long w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
-        const F8Tile tl = tiles[w % n_tiles];
+        const WorkItem tl = items[w];
         const uint32_t idesc = tl.nb == 256 ? id256 : id128;
         for (int k0 = 0; k0 < n_k && ok; k0 += chunk_k) {
           const int k1 = min(k0 + chunk_k, n_k);
@@ -283,8 +282,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int acc = 0;
     bool ok = true;
     for (long long w = blockIdx.x; w < total && ok; w += gridDim.x) {
-      const int f = (int)(w / n_tiles);
-      const F8Tile tl = tiles[w % n_tiles];
+      const WorkItem it = items[w];
+      const XengArray& arr = args.a[it.array];
+      F8Tile tl;
+      tl.c0 = it.c0;
+      tl.a0 = it.a0;
+      tl.nb = it.nb;
+      tl.pad = 0;
       for (int k0 = 0; k0 < n_k; k0 += chunk_k) {
         if (__any_sync(0xffffffffu, *abort_flag != 0)) {
           ok = false;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           break;
         }
         ptx::tc_fence_after();
-        drain_tile(tbase + acc * ACC_COLS, q, lane, half, 2, tl, f, N, npol, Bs, cross, autos);
+        drain_tile(tbase + acc * ACC_COLS, q, lane, half, 2, tl, it.f, arr.N, arr.npol, arr.Bs, arr.cross, arr.autos);
         ptx::tc_fence_before();
         ptx::mbar_arrive(&tempty[acc]);
         ++use[acc];
@@ -332,21 +336,38 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
   return cudaGetLastError();
 }
 
-cudaError_t launch_f8_xeng(const Shape& s, const CUtensorMap* tmap, int T_run, int flush_len, const F8Tile* d_tiles,
-                           int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
-                           cudaStream_t st) {
+cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(f8_xeng_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const long long total = (long long)n_tiles * s.C;
-  if (total == 0 || T_run == 0) return cudaSuccess;
-  const int grid = (int)(total < num_sms ? total : num_sms);
-  f8_xeng_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(*tmap, s.N, s.C, s.npol, s.Bs, T_run, flush_len, d_tiles,
-                                                         n_tiles, d_cross, d_autos, d_err);
+  if (args.n_items == 0 || args.T_run == 0) return cudaSuccess;
+  const int grid = (int)(args.n_items < num_sms ? args.n_items : num_sms);
+  f8_xeng_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
   return cudaGetLastError();
+}
+
+std::vector<F8Tile> f8_tile_plan(int N, int R, int plan) {
+  std::vector<F8Tile> t;
+  const int ncb = (N + 63) / 64;
+  for (int cb = 0; cb < ncb; ++cb) {
+    int a0 = 64 * cb;
+    int nb = (plan == 1 || (cb & 1)) ? 128 : 256;
+    while (a0 < N) {
+      if (2 * a0 + nb > R) nb = R - 2 * a0;
+      F8Tile x;
+      x.c0 = 64 * cb;
+      x.a0 = a0;
+      x.nb = nb;
+      x.pad = 0;
+      t.push_back(x);
+      a0 += nb / 2;
+      nb = plan == 1 ? 128 : 256;
+    }
+  }
+  return t;
 }
 
 namespace {

@@ -1,0 +1,121 @@
+"""Measurements of the secondary workloads (one JSON line each):
+
+* precision: 512 inputs x 256 channels x 65536 samples with saturation-heavy segments; tensor-core
+  X-engine time with in-chip partial sums flushed to int64 every 4096 / 16384 / 65536 samples
+  (the flush overhead is the difference to the 65536 case);
+* group: sub-arrays of 32, 64, 200, 256 and 512 inputs with 2400, 600, 300, 150 and 109 channels of
+  4096 samples: one autotuned grouped launch replayed from a CUDA graph vs separate per-array launches;
+* stream: one 512-input x 2400-channel stream and three 64-input streams in 10 ms blocks with 9 s
+  cross-power and 1 s total-power dumps over >= 100 s-equivalent; real-time factor and dump latency.
+
+    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+
+def _useful(N, C, T):
+    return N * (N + 1) // 2 * C * T
+
+
+def precision(corr, synth, torch, reps=3):
+    N, C, T, npol = 512, 256, 65536, 2
+    spec = synth.Spec(kind="saturate", seed=0x14113751 + 3, seg_len=4096, m8_segment=5)
+    x = synth.generate_device(spec, T, C, N)
+    out = {"config": "precision: N=512, C=256, T=65536, saturating segments", "flush": {}}
+    with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+        for flush in (4096, 16384, 65536):
+            xc.set_flush_period(flush)
+            xc.accumulate(x)  # warm-up
+            xc.sync()
+            xc.profile(True)
+            for _ in range(reps):
+                xc.accumulate(x)
+            ms, n = xc.profile_read(corr.CORR_KERNEL_XENG)
+            pms, _ = xc.profile_read(corr.CORR_KERNEL_UNPACK)
+            xc.profile(False)
+            xc.reset()
+            out["flush"][str(flush)] = {"xeng_ms": ms / n, "prep_ms": pms / n,
+                                        "tcmac_s": _useful(N, C, T) / (ms / n / 1e3) / 1e12}
+    base = out["flush"]["65536"]["xeng_ms"]
+    out["flush_overhead_pct"] = {k: 100.0 * (v["xeng_ms"] - base) / base for k, v in out["flush"].items()}
+    return out
+
+
+def group(corr, synth, torch, reps=5):
+    shapes = [(32, 2400), (64, 600), (200, 300), (256, 150), (512, 109)]
+    T, npol = 4096, 2
+    blocks = [synth.generate_device(synth.Spec(kind="gauss_tone", seed=0x14113751 + 4 + 100 * i), T, c, n)
+              for i, (n, c) in enumerate(shapes)]
+    useful = sum(_useful(n, c, T) for n, c in shapes)
+    st = torch.cuda.Stream()
+    res = {"config": "group: N=%s C=%s T=4096" % ([s[0] for s in shapes], [s[1] for s in shapes])}
+    with torch.cuda.stream(st), corr.Group(shapes, T, npol) as g:
+        res["tile_plans"] = g.autotune(blocks)
+        g.capture(blocks, st)
+        for name, fn in (("grouped_graph", lambda: g.launch(st)), ("grouped", lambda: g.accumulate(blocks)),
+                         ("separate", lambda: g.accumulate(blocks, separate=True))):
+            fn()
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                fn()
+            e1.record(st)
+            st.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": ms, "tcmac_s": useful / (ms / 1e3) / 1e12}
+    res["speedup_graph_vs_separate"] = res["separate"]["ms"] / res["grouped_graph"]["ms"]
+    return res
+
+
+def stream_loop(corr, synth, torch, n_blocks=10000):
+    from . import stream
+
+    specs = [stream.StreamSpec("leda512", 512, 2400, gulp_blocks=25, seed=0x14113751 + 5)]
+    specs += [stream.StreamSpec("lwa64_%d" % k, 64, 2400, gulp_blocks=25, seed=0x14113751 + 50 + k) for k in range(3)]
+    srv = stream.Server(hbm_budget_bytes=sum(s.footprint() for s in specs) + (1 << 30), keep_dumps=0)
+    try:
+        for s in specs:
+            srv.admit(s)
+        srv.admit(stream.StreamSpec("extra512", 512, 2400, gulp_blocks=25))
+        out = srv.run(n_blocks)
+    finally:
+        srv.close()
+    out["config"] = "stream: 512x2400 + 3 x 64x2400 inputs x channels, 10 ms blocks, %d blocks" % n_blocks
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", default="")
+    ap.add_argument("--stream-blocks", type=int, default=10000)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1411_3751_gb300 import corr, synth
+
+    todo = [a.only] if a.only else ["precision", "group", "stream"]
+    for name in todo:
+        if name == "precision":
+            r = precision(corr, synth, torch)
+        elif name == "group":
+            r = group(corr, synth, torch)
+        else:
+            r = stream_loop(corr, synth, torch, a.stream_blocks)
+        print(json.dumps({"measure": name, **r}))
+        sys.stdout.flush()
+
+
+if __name__ == "__main__":
+    main()

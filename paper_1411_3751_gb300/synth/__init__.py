@@ -150,25 +150,40 @@ def generate_host(spec: Spec, T: int, C: int, N: int, t0: int = 0, t_range=None,
     return out
 
 
-def generate_device(spec: Spec, T: int, C: int, N: int, t0: int = 0, out=None, stream=None):
-    """torch.uint8 cuda tensor [T][C][N] (written on the current stream)."""
+_device_tables = {}
+
+
+def _tables_on_device(spec: Spec, N: int):
+    """Tone tables and phase offsets on the device, cached per (spec, N) so launches need no sync."""
+    import torch
+
+    key = (spec.kind, spec.seed, spec.sigma, spec.sigma_hi, spec.rho, N, torch.cuda.current_device())
+    t = _device_tables.get(key)
+    if t is None:
+        lo, hi = spec.tables()
+        k = spec.phases(N)
+        t = (torch.from_numpy(lo).cuda(), torch.from_numpy(hi).cuda(), torch.from_numpy(k).cuda())
+        torch.cuda.synchronize()
+        _device_tables[key] = t
+    return t
+
+
+def generate_device(spec: Spec, T: int, C: int, N: int, t0: int = 0, out=None, stream=None, sync: bool = True):
+    """torch.uint8 cuda tensor [T][C][N] (written on the given or current stream; sync=False returns
+    without waiting for the kernel)."""
     import torch
 
     if out is None:
         out = torch.empty((T, C, N), dtype=torch.uint8, device="cuda")
-    lo, hi = spec.tables()
-    k = spec.phases(N)
-    d_lo = torch.from_numpy(lo).cuda()
-    d_hi = torch.from_numpy(hi).cuda()
-    d_k = torch.from_numpy(k).cuda()
+    d_lo, d_hi, d_k = _tables_on_device(spec, N)
     s = stream if stream is not None else torch.cuda.current_stream()
     p = spec.params()
     rc = _lib_cuda().synth_generate_device(out.data_ptr(), T, C, N, t0, ctypes.byref(p), d_lo.data_ptr(),
                                            d_hi.data_ptr(), d_k.data_ptr(), int(s.cuda_stream))
     if rc != 0:
         raise RuntimeError("synth_generate_device failed: %d" % rc)
-    # keep the tables alive until the kernel has read them
-    s.synchronize()
+    if sync:
+        s.synchronize()
     return out
 
 

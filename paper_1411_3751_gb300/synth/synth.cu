@@ -15,10 +15,14 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 __device__ __forceinline__ uint64_t draw(uint64_t s, uint64_t k) { return mix64(s + (k + 1ull) * 0x9E3779B97F4A7C15ull); }
 
+// q = floor(x / u) - 64 clipped to [-8, 7], x = noise + tone + 64 u + floor(u / 2). Outside
+// [56 u, 72 u) the clip decides; inside, x and u fit 32 bits (u is below 2^25), so the division runs
+// in 32-bit unsigned arithmetic and gives the same quotient as the 64-bit definition.
 __device__ __forceinline__ int quantise(long long noise, long long tone, long long u) {
-  long long x = noise + tone + 64 * u + u / 2;
-  long long q = x / u - 64;
-  return (int)(q < -8 ? -8 : (q > 7 ? 7 : q));
+  const long long x = noise + tone + 64 * u + u / 2;
+  if (x < 56 * u) return -8;
+  if (x >= 72 * u) return 7;
+  return (int)((unsigned)x / (unsigned)u) - 64;
 }
 
 __device__ __forceinline__ long long field_sum(uint64_t h) {
@@ -63,8 +67,8 @@ __global__ void synth_kernel(uint8_t* __restrict__ out, long long total, int C, 
 extern "C" int synth_generate_device(uint8_t* out, int T, int C, int N, long long t0, const synth_params* p,
                                      const int32_t* tab_lo, const int32_t* tab_hi, const int32_t* k, void* stream) {
   if (!out || !p || T < 0 || C < 1 || N < 1) return -1;
-  if (p->profile == SYNTH_GAUSS_TONE && (!tab_lo || !k || p->unit_lo <= 2200 || p->seg_len <= 0)) return -1;
-  if (p->profile == SYNTH_GAUSS_TONE && p->sat_period == 2 && (!tab_hi || p->unit_hi <= 2200)) return -1;
+  if (p->profile == SYNTH_GAUSS_TONE && (!tab_lo || !k || p->unit_lo <= 2200 || p->unit_lo >= (1 << 25) || p->seg_len <= 0)) return -1;
+  if (p->profile == SYNTH_GAUSS_TONE && p->sat_period == 2 && (!tab_hi || p->unit_hi <= 2200 || p->unit_hi >= (1 << 25))) return -1;
   const long long total = (long long)T * C * N;
   if (total == 0) return 0;
   long long blocks = (total + 255) / 256;

@@ -36,8 +36,8 @@ enum { SYNTH_UNIFORM = 0, SYNTH_GAUSS_TONE = 1 };
 typedef struct synth_params {
   uint64_t seed;
   int32_t profile;
-  int32_t unit_lo;     /* unit for ordinary segments (> 2200) */
-  int32_t unit_hi;     /* unit for odd segments when sat_period == 2 (> 2200) */
+  int32_t unit_lo;     /* unit for ordinary segments (2200 < unit < 2^25) */
+  int32_t unit_hi;     /* unit for odd segments when sat_period == 2 (2200 < unit < 2^25) */
   int32_t sat_period;  /* 0: single unit; 2: alternate segments */
   int32_t seg_len;     /* samples per segment (> 0) */
   int32_t m8_segment;  /* index of the all -8-8i segment, or -1 */

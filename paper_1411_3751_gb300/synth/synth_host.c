@@ -31,8 +31,8 @@ int synth_generate_host(uint8_t* out, int t_begin, int t_count, int c_begin, int
                         long long t0, const synth_params* p, const int32_t* tab_lo, const int32_t* tab_hi,
                         const int32_t* k) {
   if (!out || !p || C < 1 || N < 1 || t_count < 0 || c_count < 0 || c_begin < 0 || c_begin + c_count > C) return -1;
-  if (p->profile == SYNTH_GAUSS_TONE && (!tab_lo || !k || p->unit_lo <= 2200 || p->seg_len <= 0)) return -1;
-  if (p->profile == SYNTH_GAUSS_TONE && p->sat_period == 2 && (!tab_hi || p->unit_hi <= 2200)) return -1;
+  if (p->profile == SYNTH_GAUSS_TONE && (!tab_lo || !k || p->unit_lo <= 2200 || p->unit_lo >= (1 << 25) || p->seg_len <= 0)) return -1;
+  if (p->profile == SYNTH_GAUSS_TONE && p->sat_period == 2 && (!tab_hi || p->unit_hi <= 2200 || p->unit_hi >= (1 << 25))) return -1;
   for (int tt = 0; tt < t_count; ++tt) {
     const long long t = t0 + t_begin + tt;
     for (int cc = 0; cc < c_count; ++cc) {

@@ -10,7 +10,7 @@ are resident in HBM before timing; they exceed L2, so no flush is needed between
 Prints ONE JSON line (rank 0). Metric: useful Tera-CMAC/s = N (N + 1) / 2 * C * T / time / 1e12, plus
 the real-time factor at the 24.0 kHz channel rate. `--impl reference` times the CPU oracle instead.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--path fp8tc|fp32] [--impl reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--path fp8tc|i8mma|fp32] [--impl reference]
 Multi-GPU: launched by torch.distributed.run; channels are independent, every rank runs the same
 per-GPU workload on its own GPU (weak scaling), no data-path collective.
 """
@@ -224,10 +224,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp8tc_fused", "fp32"])
+    ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp8tc_fused", "i8mma", "fp32"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--i8-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -301,6 +302,10 @@ def main():
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_note = "%s bf16 sustained x 2 (nominal fp8/bf16 ratio)" % peak_src
         bound = "tensor"
+    elif args.path == "i8mma":
+        peak = 158.0  # mma.sync m16n8k32 s8 throughput measured by a microbenchmark on this GPU
+        peak_note = "mma.sync s8 microbenchmark (TOP/s)"
+        bound = "tensor"
     else:
         peak = 77.9  # FP32 FMA peak measured by a microbenchmark on this GPU at 1.95 GHz
         peak_note = "FP32 FMA microbenchmark (152 SMs x 128 lanes x 2 flop)"
@@ -310,7 +315,8 @@ def main():
     if args.path == "fp8tc" and abs(blocks_per_launch - 1.0) < 1e-9:
         traffic = profiled_traffic(["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"], "f8_xeng_512in_128ch_8192.md")
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel"}.get(args.path, "xeng_fp32_kernel"),
+            "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel",
+                                           "i8mma": "xeng_i8mma_kernel"}.get(args.path, "xeng_fp32_kernel"),
             "peak_source": peak_note, "launch_ms": per_launch_ms,
             "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop (%.0f blocks of 8192 samples per launch)"
                            % (flops_launch, blocks_per_launch)}
@@ -344,22 +350,27 @@ def main():
                "ms_per_step": e_ms / args.e2e_steps}
         del host_blocks
 
-    # same-GPU FP32 path on the same workload (comparison leg of the metric)
-    fp32 = None
-    if args.path.startswith("fp8tc") and args.fp32_steps > 0:
-        xc.set_path("fp32")
+    # same-GPU comparison legs of the metric on the same workload: the integer tensor path
+    # (mma.sync s8) and the FP32 CUDA-core path (the paper's arithmetic)
+    def path_leg(path, n_steps):
+        if not args.path.startswith("fp8tc") or n_steps <= 0:
+            return None
+        xc.set_path(path)
         step()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.fp32_steps):
+        for _ in range(n_steps):
             step()
         f1.record(stream)
         torch.cuda.synchronize()
-        f_ms = max_over_ranks(f0.elapsed_time(f1), world) / args.fp32_steps
-        fp32 = {"value": cm_step * world / (f_ms / 1e3) / 1e12, "unit": "Tera-CMAC/s", "ms_per_step": f_ms,
-                "real_time_factor": (T_BLOCK * N_BLOCKS / CHANNEL_RATE_HZ) / (f_ms / 1e3)}
+        f_ms = max_over_ranks(f0.elapsed_time(f1), world) / n_steps
         xc.set_path(args.path)
+        return {"value": cm_step * world / (f_ms / 1e3) / 1e12, "unit": "Tera-CMAC/s", "ms_per_step": f_ms,
+                "real_time_factor": (T_BLOCK * N_BLOCKS / CHANNEL_RATE_HZ) / (f_ms / 1e3), "steps": n_steps}
+
+    i8 = path_leg("i8mma", args.i8_steps)
+    fp32 = path_leg("fp32", args.fp32_steps)
     xc.sync()
     xc.close()
 
@@ -372,7 +383,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "Tera-CMAC/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3" if args.path.startswith("fp8tc") else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"i8mma": "s8", "fp32": "f32"}.get(args.path, "e4m3"), "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN, "n_time_per_block": T_BLOCK,
                        "blocks_per_step": N_BLOCKS, "n_pol": N_POL, "path": args.path,
                        "l2": "inputs 8 GiB > L2, no flush needed", "parallelism": "channels per GPU (replicas)"},
@@ -384,6 +395,7 @@ def main():
             "gpu_launches_per_step": launches_per_step,
             "clocks": clk,
             "e2e": e2e,
+            "i8mma_path": i8,
             "fp32_path": fp32,
             "cpu_baseline": cpu,
         }

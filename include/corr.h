@@ -60,9 +60,12 @@ typedef enum corr_status {
 typedef enum corr_path {
   CORR_PATH_AUTO = 0,  /* fastest available: FP8 tensor path on sm_103a */
   CORR_PATH_FP32 = 1,  /* FP32 FMA on CUDA cores (the arithmetic the paper's K20X X-engine used, Sec. 2.5) */
+  CORR_PATH_I8MMA = 2, /* warp-level integer MMA (mma.sync s8 x s8 -> s32) on sign-extended nibbles,
+                          unpacked in shared memory inside the kernel; the integer tensor path */
   CORR_PATH_FP8TC = 3, /* tcgen05 kind::f8f6f4 (e4m3 operands, FP32 accumulation in TMEM): an
-                          unpack pass builds the operand in device scratch, a TMA-fed persistent
-                          kernel multiplies; the total-power kernel runs alongside. The default. */
+                          unpack pass builds the offset operand and the per-input sums in device
+                          scratch, a TMA-fed persistent kernel multiplies and adds the autos from its
+                          diagonal. The default. */
   CORR_PATH_FP8TC_FUSED = 4 /* same arithmetic with the unpack done inside the X-engine by converter
                                warps (no scratch; slower on this input layout, kept for comparison) */
 } corr_path;
@@ -85,8 +88,9 @@ typedef enum corr_kernel {
  * n_time_per_block samples per channel (T), n_pol polarisations per station (1 or 2).
  * Sec. 2.5: data are read in groups of 8000 spectra; T is that group size here.
  * Allocates and zeroes the int64 accumulators and the path scratch on the current device.
- * Returns NULL on error (corr_last_error). Rejects N < 1, C < 1, T < 1, n_pol not 1/2,
- * N % n_pol != 0, sizes whose byte counts overflow, and footprints above free device memory (OOM).
+ * Returns NULL on error (corr_last_error). Rejects N < 1 or N > 2^20, C < 1 or C > 65535, T < 1,
+ * n_pol not 1/2, N % n_pol != 0, sizes whose byte counts overflow, and footprints above free device
+ * memory (OOM).
  */
 corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol);
 

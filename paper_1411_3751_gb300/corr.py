@@ -15,12 +15,13 @@ LIB_PATH = os.path.join(_PKG, "_build", "libcorr.so")
 
 CORR_OK = 0
 CORR_ERR_ARG, CORR_ERR_CUDA, CORR_ERR_OOM, CORR_ERR_STATE, CORR_ERR_TIMEOUT, CORR_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-CORR_PATH_AUTO, CORR_PATH_FP32, CORR_PATH_FP8TC, CORR_PATH_FP8TC_FUSED = 0, 1, 3, 4
+CORR_PATH_AUTO, CORR_PATH_FP32, CORR_PATH_I8MMA, CORR_PATH_FP8TC, CORR_PATH_FP8TC_FUSED = 0, 1, 2, 3, 4
 CORR_WHAT_CROSS, CORR_WHAT_AUTO = 1, 2
 CORR_FMT_CI64, CORR_FMT_CF32, CORR_FMT_CF32_NORM = 0, 1, 2
 CORR_KERNEL_XENG, CORR_KERNEL_UNPACK, CORR_KERNEL_AUTOS, CORR_KERNEL_DUMP = 0, 1, 2, 3
 
-PATHS = {"auto": CORR_PATH_AUTO, "fp32": CORR_PATH_FP32, "fp8tc": CORR_PATH_FP8TC, "fp8tc_fused": CORR_PATH_FP8TC_FUSED}
+PATHS = {"auto": CORR_PATH_AUTO, "fp32": CORR_PATH_FP32, "i8mma": CORR_PATH_I8MMA, "fp8tc": CORR_PATH_FP8TC,
+         "fp8tc_fused": CORR_PATH_FP8TC_FUSED}
 
 # (name, restype, argtypes) of every symbol include/corr.h declares
 _c_int, _c_ll, _c_sz, _c_vp, _c_cp = ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p

@@ -52,7 +52,7 @@ Layout make_layout(int N, int C, int T, int npol) {
   Layout L{};
   L.ok = false;
   if (N < 1 || C < 1 || T < 1 || (npol != 1 && npol != 2) || N % npol != 0) return L;
-  if (N > (1 << 20)) return L;
+  if (N > (1 << 20) || C > 65535) return L;  // channels index grid.y of the per-channel kernels
   L.s.N = N;
   L.s.C = C;
   L.s.T = T;
@@ -159,7 +159,8 @@ namespace {
 int resolved_path(const corr_ctx* c) { return c->path == CORR_PATH_AUTO ? CORR_PATH_FP8TC : c->path; }
 
 bool valid_path(int path) {
-  return path == CORR_PATH_AUTO || path == CORR_PATH_FP32 || path == CORR_PATH_FP8TC || path == CORR_PATH_FP8TC_FUSED;
+  return path == CORR_PATH_AUTO || path == CORR_PATH_FP32 || path == CORR_PATH_I8MMA || path == CORR_PATH_FP8TC ||
+         path == CORR_PATH_FP8TC_FUSED;
 }
 
 int flush_for(const corr_ctx* c, int path) {
@@ -239,6 +240,11 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
     e = launch_fp32(c->L.s, d_in, T_blk, flush, c->d_tiles32, c->n_tiles32, c->d_cross, c->d_autos, st);
     timer_end(c, CORR_KERNEL_XENG, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "fp32 x-engine launch");
+  } else if (path == CORR_PATH_I8MMA) {
+    const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
+    e = launch_i8mma(c->L.s, d_in, T_blk, flush, c->d_tiles32, c->n_tiles32, c->d_cross, c->d_autos, st);
+    timer_end(c, CORR_KERNEL_XENG, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "int8 mma x-engine launch");
   } else {
     // tensor paths: one pass builds the operand (two-pass path) and the per-input offset sums for
     // both cadences; the X-engine adds the offset-domain products and their diagonal.
@@ -386,8 +392,8 @@ size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int
 corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol) {
   const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
   if (!L.ok) {
-    fail(CORR_ERR_ARG, "corr_create: invalid shape (need N >= 1, C >= 1, T >= 1, n_pol in {1,2}, N % n_pol == 0, "
-                       "sizes within range)");
+    fail(CORR_ERR_ARG, "corr_create: invalid shape (need 1 <= N <= 2^20, 1 <= C <= 65535, T >= 1, n_pol in {1,2}, "
+                       "N % n_pol == 0, sizes within range)");
     return nullptr;
   }
   int dev = 0;

@@ -97,6 +97,8 @@ cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long lo
                          cudaStream_t st);
 
 // Fused unpack + tcgen05 X-engine (offset-domain products into d_cross, diagonal into d_autos).
+cudaError_t launch_i8mma(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const int2* d_tiles,
+                         int n_tiles, long long* d_cross, long long* d_autos, cudaStream_t st);
 cudaError_t launch_f8_fused(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const F8Tile* d_tiles,
                             int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
                             cudaStream_t st);

@@ -54,13 +54,16 @@ def test_host_only_helpers(lib):
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_AUTO) == fp
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP32) < fp
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP8TC_FUSED) < fp
+    assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_I8MMA) < fp  # no operand scratch
+    assert lib.corr_footprint_bytes(4, 65536, 1, 2, lib.CORR_PATH_FP32) == 0     # channel limit
     assert lib.corr_footprint_bytes(0, 1, 1, 1, 0) == 0
     assert lib.corr_footprint_bytes(3, 1, 1, 2, 0) == 0
     assert lib.corr_footprint_bytes(4, 1, 1, 2, 99) == 0
     assert "sm_103a" in lib.corr_version()
 
 
-@pytest.mark.parametrize("args", [(0, 1, 1, 1), (4, 0, 1, 2), (4, 1, 0, 2), (5, 1, 1, 2), (4, 1, 1, 3), (-2, 1, 1, 1)])
+@pytest.mark.parametrize("args", [(0, 1, 1, 1), (4, 0, 1, 2), (4, 1, 0, 2), (5, 1, 1, 2), (4, 1, 1, 3), (-2, 1, 1, 1),
+                                  (4, 65536, 1, 2), ((1 << 20) + 2, 1, 1, 2)])
 def test_create_rejects_bad_shapes(lib, args):
     with pytest.raises(lib.CorrError) as ei:
         lib.corr_create(*args)

@@ -11,7 +11,7 @@ from oracle import oracle
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["fp32", "fp8tc", "fp8tc_fused"]
+PATHS = ["fp32", "i8mma", "fp8tc", "fp8tc_fused"]
 
 
 @pytest.fixture(scope="module")
@@ -240,14 +240,15 @@ def _freivalds(x_bytes, V_cross, npol, rng, chunk=16384):
     return np.array_equal(Vw.real, zr) and np.array_equal(Vw.imag, zi)
 
 
-def test_full_size_512_inputs_128_channels_fp8(env):
+@pytest.mark.parametrize("path", ["fp8tc", "i8mma"])
+def test_full_size_512_inputs_128_channels(env, path):
     """N=512, C=128, 16 blocks of 8192 samples (the benchmark's configuration and launch sequence):
     sampled cells against the oracle on host-regenerated channels, all autos, Freivalds projections on
     every channel, and the auto-station invariants."""
     corr, synth, torch = env
     N, C, T, B, npol = 512, 128, 8192, 16, 2
     spec = synth.Spec(kind="gauss_tone", seed=0x14113751 + 2)
-    xc = corr.Correlator(N, C, T, npol, path="fp8tc")
+    xc = corr.Correlator(N, C, T, npol, path=path)
     host_all = np.empty((B * T, C, N), dtype=np.uint8)
     blocks = []
     for b in range(B):

@@ -1,8 +1,9 @@
 """Measurements of the secondary workloads (one JSON line each):
 
-* precision: 512 inputs x 256 channels x 65536 samples with saturation-heavy segments; tensor-core
-  X-engine time with in-chip partial sums flushed to int64 every 4096 / 16384 / 65536 samples
-  (the flush overhead is the difference to the 65536 case);
+* precision: 512 inputs x 256 channels x 65536 samples with saturation-heavy segments; X-engine time
+  with in-chip partial sums flushed to int64 every 4096 / 16384 / 65536 samples on the FP8 tcgen05
+  path and every 16384 / 65536 samples on the int8 mma.sync path (the flush overhead is the
+  difference to the 65536 case);
 * group: sub-arrays of 32, 64, 200, 256 and 512 inputs with 2400, 600, 300, 150 and 109 channels of
   4096 samples: one autotuned grouped launch replayed from a CUDA graph vs separate per-array launches;
 * stream: one 512-input x 2400-channel stream and three 64-input streams in 10 ms blocks with 9 s
@@ -26,23 +27,26 @@ def precision(corr, synth, torch, reps=3):
     N, C, T, npol = 512, 256, 65536, 2
     spec = synth.Spec(kind="saturate", seed=0x14113751 + 3, seg_len=4096, m8_segment=5)
     x = synth.generate_device(spec, T, C, N)
-    out = {"config": "precision: N=512, C=256, T=65536, saturating segments", "flush": {}}
-    with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
-        for flush in (4096, 16384, 65536):
-            xc.set_flush_period(flush)
-            xc.accumulate(x)  # warm-up
-            xc.sync()
-            xc.profile(True)
-            for _ in range(reps):
-                xc.accumulate(x)
-            ms, n = xc.profile_read(corr.CORR_KERNEL_XENG)
-            pms, _ = xc.profile_read(corr.CORR_KERNEL_UNPACK)
-            xc.profile(False)
-            xc.reset()
-            out["flush"][str(flush)] = {"xeng_ms": ms / n, "prep_ms": pms / n,
-                                        "tcmac_s": _useful(N, C, T) / (ms / n / 1e3) / 1e12}
-    base = out["flush"]["65536"]["xeng_ms"]
-    out["flush_overhead_pct"] = {k: 100.0 * (v["xeng_ms"] - base) / base for k, v in out["flush"].items()}
+    out = {"config": "precision: N=512, C=256, T=65536, saturating segments"}
+    for path, flushes in (("fp8tc", (4096, 16384, 65536)), ("i8mma", (16384, 65536))):
+        res = {}
+        with corr.Correlator(N, C, T, npol, path=path) as xc:
+            for flush in flushes:
+                xc.set_flush_period(flush)
+                xc.accumulate(x)  # warm-up
+                xc.sync()
+                xc.profile(True)
+                for _ in range(reps):
+                    xc.accumulate(x)
+                ms, n = xc.profile_read(corr.CORR_KERNEL_XENG)
+                pms, _ = xc.profile_read(corr.CORR_KERNEL_UNPACK)
+                xc.profile(False)
+                xc.reset()
+                res[str(flush)] = {"xeng_ms": ms / n, "prep_ms": pms / n,
+                                   "tcmac_s": _useful(N, C, T) / (ms / n / 1e3) / 1e12}
+        base = res["65536"]["xeng_ms"]
+        out[path] = {"flush": res,
+                     "flush_overhead_pct": {k: 100.0 * (v["xeng_ms"] - base) / base for k, v in res.items()}}
     return out
 
 

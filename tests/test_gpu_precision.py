@@ -1,7 +1,8 @@
 """Precision variants at 512 inputs x 256 channels x 65536 samples with saturation-heavy segments
-(alternating 4096-sample segments at sigma = 6 and one all -8-8i segment): the tensor path with
-in-chip partial sums flushed to int64 every 4096 samples and once per 65536 samples, both bit-exact
-(sampled oracle cells on host-regenerated channels, oracle autos, and agreement between the two)."""
+(alternating 4096-sample segments at sigma = 6 and one all -8-8i segment): the FP8 tensor path with
+in-chip partial sums flushed to int64 every 4096 samples and once per 65536 samples, and the int8
+mma.sync path flushed every 16384 samples, all bit-exact (sampled oracle cells on host-regenerated
+channels, oracle autos, and agreement between the three)."""
 import numpy as np
 import pytest
 
@@ -29,15 +30,17 @@ def test_flush_periods_saturating_input(env):
     spec = synth.Spec(kind="saturate", seed=0x14113751 + 3, seg_len=4096, m8_segment=5)
     x = synth.generate_device(spec, T, C, N)
     results = {}
-    for flush in (4096, 65536):
-        with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+    for path, flush in (("fp8tc", 4096), ("fp8tc", 65536), ("i8mma", 16384)):
+        with corr.Correlator(N, C, T, npol, path=path) as xc:
             xc.set_flush_period(flush)
             xc.accumulate(x)
-            results[flush] = (xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy(), xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy())
+            results[path, flush] = (xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy(),
+                                    xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy())
             xc.sync()
-    assert np.array_equal(results[4096][0], results[65536][0])
-    assert np.array_equal(results[4096][1], results[65536][1])
-    cross, autos = results[4096]
+    for key in (("fp8tc", 65536), ("i8mma", 16384)):
+        assert np.array_equal(results["fp8tc", 4096][0], results[key][0]), key
+        assert np.array_equal(results["fp8tc", 4096][1], results[key][1]), key
+    cross, autos = results["fp8tc", 4096]
     rng = np.random.default_rng(33)
     for f in (0, 200):
         hf = synth.generate_host(spec, T, C, N, c_range=(f, f + 1))

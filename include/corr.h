@@ -88,9 +88,9 @@ typedef enum corr_kernel {
  * n_time_per_block samples per channel (T), n_pol polarisations per station (1 or 2).
  * Sec. 2.5: data are read in groups of 8000 spectra; T is that group size here.
  * Allocates and zeroes the int64 accumulators and the path scratch on the current device.
- * Returns NULL on error (corr_last_error). Rejects N < 1 or N > 2^20, C < 1 or C > 65535, T < 1,
- * n_pol not 1/2, N % n_pol != 0, sizes whose byte counts overflow, and footprints above free device
- * memory (OOM).
+ * Returns NULL on error (corr_last_error). Rejects N < 1, B_s n_pol^2 >= 2^31 station-pair
+ * products per channel (N > 65534 for n_pol = 2), C < 1 or C > 65535, T < 1, n_pol not 1/2,
+ * N % n_pol != 0, sizes whose byte counts overflow, and footprints above free device memory (OOM).
  */
 corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol);
 
@@ -151,6 +151,27 @@ int corr_accumulate_autos(corr_ctx* ctx, const void* d_samples, void* cuda_strea
  * 1 s total-power cadence runs independently of the 9 s cross-power cadence).
  */
 int corr_dump(corr_ctx* ctx, void* out, int is_device_ptr, int what, int fmt, int reset, void* cuda_stream);
+
+/*
+ * corr_dump_stations - dump, and with reset != 0 zero, only the cells among a list of stations
+ * (Sec. 2.6: the total power of the outrigger antennas is integrated for 1 s while the visibilities
+ * integrate for 9 s, by selectively zeroing and dumping cells of the correlation accumulator).
+ * stations: HOST array of n_stations distinct station indices in [0, S), S = n_inputs / n_pol, in any
+ * order; read during the call only. Output (device pointer if is_device_ptr, else host; format as
+ * corr_dump):
+ *   CORR_WHAT_AUTO:  [C][n_stations][n_pol]: autos of input stations[k] * n_pol + p;
+ *   CORR_WHAT_CROSS: [C][n_stations (n_stations + 1) / 2][n_pol^2][2]: list pair (k, l), k >= l, at
+ *                    index k (k + 1) / 2 + l, products (p, q) in matrix order, element
+ *                    sum_t x_{stations[k] p}(t) conj(x_{stations[l] q}(t)) (the conjugate of the stored
+ *                    cell when stations[k] < stations[l]).
+ * With reset, only these cells restart from zero; every other cell keeps integrating. Each cell's
+ * sample count is counted from its own last reset (full or selective), and CF32_NORM divides by it;
+ * corr_samples_accumulated keeps counting from the last full reset. Errors: CORR_ERR_ARG for an empty,
+ * out-of-range or repeated station list, CORR_ERR_OOM if the small per-cell count array cannot be
+ * allocated (first selective reset only).
+ */
+int corr_dump_stations(corr_ctx* ctx, const int* stations, int n_stations, void* out, int is_device_ptr, int what,
+                       int fmt, int reset, void* cuda_stream);
 
 /* Samples per channel accumulated into `what` since creation or its last reset (host-side count). */
 long long corr_samples_accumulated(const corr_ctx* ctx, int what);

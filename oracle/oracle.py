@@ -11,7 +11,11 @@ Sec. 2.6, the auto-correlation cells; Sec. 2.2, samples requantised to 4+4 bits)
 * sample byte = (Re nibble << 4) | Im nibble, each nibble a 4-bit two's-complement integer;
 * ``cross[f, b(a, c), p * n_pol + q] = sum_t x_{a p}(t) conj(x_{c q}(t))`` for stations a >= c,
   ``b(a, c) = a (a + 1) / 2 + c``, stored as int64 (re, im);
-* ``autos[f, m] = sum_t |x_m(t)|^2``.
+* ``autos[f, m] = sum_t |x_m(t)|^2``;
+* selected stations (Sec. 2.6, cells of chosen antennas dumped and zeroed on their own cadence), for
+  a station list st: ``station_cross[f, k (k + 1) / 2 + l, p * n_pol + q] =
+  sum_t x_{st[k] p}(t) conj(x_{st[l] q}(t))`` for list positions k >= l, and
+  ``station_autos[f, k, p] = autos[f, st[k] n_pol + p]``.
 
 Dump formats (the paper stores visibilities as 32-bit floats after averaging, Sec. 2.5; the
 integer sum is the exact product, so two float views are defined on top of it):
@@ -121,6 +125,29 @@ def autos(samples: np.ndarray) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle_autos failed: %d" % rc)
     return out
+
+
+def station_cross(samples: np.ndarray, stations, n_pol: int) -> np.ndarray:
+    """Cross cells among a station list, ``[C][n (n + 1) / 2][n_pol^2][2]`` int64, by the cell definition."""
+    samples = _check_samples(samples)
+    C = samples.shape[1]
+    st = [int(v) for v in stations]
+    cl = []
+    for f in range(C):
+        for k in range(len(st)):
+            for l in range(k + 1):
+                for p in range(n_pol):
+                    for q in range(n_pol):
+                        cl.append((f, st[k] * n_pol + p, st[l] * n_pol + q))
+    npairs = len(st) * (len(st) + 1) // 2
+    return cells(samples, cl).reshape(C, npairs, n_pol * n_pol, 2)
+
+
+def station_autos(samples: np.ndarray, stations, n_pol: int) -> np.ndarray:
+    """Autocorrelations of the inputs of a station list, ``[C][n][n_pol]`` int64."""
+    a = autos(samples)
+    idx = [int(s) * n_pol + p for s in stations for p in range(n_pol)]
+    return a[:, idx].reshape(a.shape[0], len(stations), n_pol)
 
 
 def to_format(values: np.ndarray, fmt: int, n_samples: int) -> np.ndarray:

@@ -35,6 +35,7 @@ SIGNATURES = [
     ("corr_accumulate_host", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_accumulate_autos", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_dump", _c_int, [_c_vp, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
+    ("corr_dump_stations", _c_int, [_c_vp, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
     ("corr_samples_accumulated", _c_ll, [_c_vp, _c_int]),
     ("corr_reset", _c_int, [_c_vp, _c_int, _c_vp]),
     ("corr_sync", _c_int, [_c_vp, _c_vp]),
@@ -123,6 +124,16 @@ def corr_accumulate_autos(ctx: int, d_samples: int, stream: int) -> int:
 
 def corr_dump(ctx: int, out: int, is_device_ptr: int, what: int, fmt: int, reset: int, stream: int) -> int:
     return _check(_lib.corr_dump(ctx, out, is_device_ptr, what, fmt, reset, stream), "corr_dump")
+
+
+def corr_dump_stations(ctx: int, stations, n_stations: int, out: int, is_device_ptr: int, what: int, fmt: int,
+                       reset: int, stream: int) -> int:
+    """`stations`: a host int32 buffer address (or a sequence of ints, marshalled here)."""
+    if not isinstance(stations, int):
+        arr = (ctypes.c_int * len(stations))(*[int(v) for v in stations])
+        stations = ctypes.addressof(arr)
+    return _check(_lib.corr_dump_stations(ctx, stations, n_stations, out, is_device_ptr, what, fmt, reset, stream),
+                  "corr_dump_stations")
 
 
 def corr_samples_accumulated(ctx: int, what: int) -> int:
@@ -294,6 +305,27 @@ class Correlator:
             raise ValueError("bad output tensor")
         corr_dump(self.ctx, out.data_ptr(), 1 if out.is_cuda else 0, what, fmt, 1 if reset else 0,
                   _stream_handle(stream))
+        return out
+
+    def station_out_shape(self, what: int, n_stations: int):
+        if what == CORR_WHAT_CROSS:
+            return (self.n_chans, n_stations * (n_stations + 1) // 2, self.n_pol * self.n_pol, 2)
+        return (self.n_chans, n_stations, self.n_pol)
+
+    def dump_stations(self, stations, what: int = CORR_WHAT_AUTO, fmt: int = CORR_FMT_CI64, reset: bool = False,
+                      out=None, device: bool = True, stream=None):
+        """Snapshot (and with reset, zero) only the cells among `stations` (a list of station indices)."""
+        import torch
+
+        stations = [int(v) for v in stations]
+        dtype = torch.int64 if fmt == CORR_FMT_CI64 else torch.float32
+        shape = self.station_out_shape(what, len(stations))
+        if out is None:
+            out = torch.empty(shape, dtype=dtype, device="cuda" if device else "cpu", pin_memory=(not device))
+        if out.dtype != dtype or tuple(out.shape) != shape or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        corr_dump_stations(self.ctx, stations, len(stations), out.data_ptr(), 1 if out.is_cuda else 0, what, fmt,
+                           1 if reset else 0, _stream_handle(stream))
         return out
 
     def reset(self, what: int = CORR_WHAT_CROSS | CORR_WHAT_AUTO, stream=None):

@@ -104,6 +104,33 @@ __device__ __forceinline__ void pair_of(int b, int& sa, int& sc) {
   sc = b - (int)((long long)a * (a + 1) / 2);
 }
 
+// Corrected value of cross cell `cell` (= f * B_s * P + b * P + pidx) from its raw int64 sums.
+__device__ __forceinline__ void cross_value(const long long* __restrict__ acc, long long cell, long long f, int b,
+                                            int pidx, const Shape2& g, long long& re, long long& im) {
+  const longlong2 v2 = reinterpret_cast<const longlong2*>(acc)[cell];
+  re = v2.x;
+  im = v2.y;
+  if (g.soff != nullptr && g.t_off != 0) {
+    int sa, sc;
+    pair_of(b, sa, sc);
+    const long long a = (long long)sa * g.npol + pidx / g.npol;
+    const long long c = (long long)sc * g.npol + pidx % g.npol;
+    const longlong2 s_a = reinterpret_cast<const longlong2*>(g.soff)[f * g.N + a];
+    const longlong2 s_c = reinterpret_cast<const longlong2*>(g.soff)[f * g.N + c];
+    re += -8 * (s_a.x + s_a.y + s_c.x + s_c.y) + 128 * g.t_off;
+    im += -8 * (s_a.y - s_a.x + s_c.x - s_c.y);
+  }
+}
+
+__device__ __forceinline__ long long auto_value(const long long* __restrict__ acc, long long k, const Shape2& g) {
+  long long v = acc[k];
+  if (g.soff != nullptr && g.t_off != 0) {
+    const longlong2 s = reinterpret_cast<const longlong2*>(g.soff)[k];
+    v += -16 * (s.x + s.y) + 128 * g.t_off;  // A = Au - 16 (Re s + Im s) + 128 T
+  }
+  return v;
+}
+
 // Cross dump of cells [cell0, cell0 + n_cells) (a cell = one (re, im) pair), output indexed from 0.
 __global__ void dump_cross_kernel(const long long* __restrict__ acc, long long cell0, long long n_cells,
                                   void* __restrict__ out, int fmt, long long n_samples, Shape2 g) {
@@ -111,23 +138,14 @@ __global__ void dump_cross_kernel(const long long* __restrict__ acc, long long c
   const int lp = g.P == 4 ? 2 : 0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_cells; k += (long long)gridDim.x * blockDim.x) {
     const long long cell = cell0 + k;
-    const longlong2 v2 = reinterpret_cast<const longlong2*>(acc)[cell];
-    long long re = v2.x, im = v2.y;
-    if (g.soff != nullptr && g.t_off != 0) {
-      const long long f = cell / cpc;
-      const int r = (int)(cell - f * cpc);
-      const int b = r >> lp, pidx = r & (g.P - 1);
-      int sa, sc;
-      pair_of(b, sa, sc);
-      const long long a = (long long)sa * g.npol + pidx / g.npol;
-      const long long c = (long long)sc * g.npol + pidx % g.npol;
-      const longlong2 s_a = reinterpret_cast<const longlong2*>(g.soff)[f * g.N + a];
-      const longlong2 s_c = reinterpret_cast<const longlong2*>(g.soff)[f * g.N + c];
-      re += -8 * (s_a.x + s_a.y + s_c.x + s_c.y) + 128 * g.t_off;
-      im += -8 * (s_a.y - s_a.x + s_c.x - s_c.y);
-    }
-    put<void>(out, 2 * k, re, fmt, n_samples);
-    put<void>(out, 2 * k + 1, im, fmt, n_samples);
+    const long long f = cell / cpc;
+    const int r = (int)(cell - f * cpc);
+    const int b = r >> lp, pidx = r & (g.P - 1);
+    long long re, im;
+    cross_value(acc, cell, f, b, pidx, g, re, im);
+    const long long ns = g.base ? n_samples - g.base[b] : n_samples;
+    put<void>(out, 2 * k, re, fmt, ns);
+    put<void>(out, 2 * k + 1, im, fmt, ns);
   }
 }
 
@@ -135,12 +153,74 @@ __global__ void dump_cross_kernel(const long long* __restrict__ acc, long long c
 __global__ void dump_autos_kernel(const long long* __restrict__ acc, long long k0, long long n, void* __restrict__ out,
                                   int fmt, long long n_samples, Shape2 g) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    long long v = acc[k0 + k];
-    if (g.soff != nullptr && g.t_off != 0) {
-      const longlong2 s = reinterpret_cast<const longlong2*>(g.soff)[k0 + k];
-      v += -16 * (s.x + s.y) + 128 * g.t_off;  // A = Au - 16 (Re s + Im s) + 128 T
+    const long long v = auto_value(acc, k0 + k, g);
+    const long long ns = g.base ? n_samples - g.base[(k0 + k) % g.N] : n_samples;
+    put<void>(out, k, v, fmt, ns);
+  }
+}
+
+// Selective dump (Sec. 2.6: selected cells are dumped and zeroed at their own cadence). Cross: unit =
+// (channel, list pair k >= l, product p q) -> sum x_{st[k] p} conj(x_{st[l] q}); the stored cell is
+// (st[k] p, st[l] q) when st[k] >= st[l], else its conjugate (st[l] q, st[k] p). Autos: unit =
+// (channel, list position k, pol p) -> input st[k] n_pol + p. A reset stores minus the corrected
+// value's offset-domain correction, acc := acc - value, so the corrected value restarts from zero
+// while the shared offset sums keep integrating (the correction is affine in them).
+__global__ void dump_select_kernel(long long* __restrict__ acc, const int* __restrict__ st, int n_st, int f0, int nf,
+                                   void* __restrict__ out, int fmt, long long n_samples, int reset, Shape2 g) {
+  if (g.autos) {
+    const long long per = (long long)n_st * g.npol;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < (long long)nf * per;
+         u += (long long)gridDim.x * blockDim.x) {
+      const long long fl = u / per;
+      const int r = (int)(u - fl * per);
+      const int i = st[r / g.npol] * g.npol + r % g.npol;
+      const long long k = (f0 + fl) * g.N + i;
+      const long long v = auto_value(acc, k, g);
+      put<void>(out, u, v, fmt, g.base ? n_samples - g.base[i] : n_samples);
+      if (reset) acc[k] -= v;
     }
-    put<void>(out, k, v, fmt, n_samples);
+    return;
+  }
+  const long long npairs = (long long)n_st * (n_st + 1) / 2;
+  const long long per = npairs * g.P;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < (long long)nf * per;
+       u += (long long)gridDim.x * blockDim.x) {
+    const long long fl = u / per;
+    const int r = (int)(u - fl * per);
+    const int pr = r / g.P, pidx = r % g.P;
+    int k, l;
+    pair_of(pr, k, l);
+    const int a = st[k], c = st[l], p = pidx / g.npol, q = pidx % g.npol;
+    const bool swap = a < c;
+    const int sa = swap ? c : a, sc = swap ? a : c;
+    const int sp = swap ? q * g.npol + p : pidx;  // stored product index
+    const int b = sa * (sa + 1) / 2 + sc;
+    const long long f = f0 + fl;
+    const long long cell = (f * g.Bs + b) * g.P + sp;
+    long long re, im;
+    cross_value(acc, cell, f, b, sp, g, re, im);
+    const long long ns = g.base ? n_samples - g.base[b] : n_samples;
+    put<void>(out, 2 * u, re, fmt, ns);
+    put<void>(out, 2 * u + 1, swap ? -im : im, fmt, ns);
+    if (reset) {
+      acc[2 * cell] -= re;
+      acc[2 * cell + 1] -= im;
+    }
+  }
+}
+
+__global__ void set_base_kernel(long long* __restrict__ base, const int* __restrict__ st, int n_st, long long value,
+                                int npol, int autos) {
+  const long long n = autos ? (long long)n_st * npol : (long long)n_st * (n_st + 1) / 2;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+    if (autos) {
+      base[st[u / npol] * npol + u % npol] = value;
+    } else {
+      int k, l;
+      pair_of((int)u, k, l);
+      const int a = st[k] > st[l] ? st[k] : st[l], c = st[k] > st[l] ? st[l] : st[k];
+      base[a * (a + 1) / 2 + c] = value;
+    }
   }
 }
 
@@ -151,6 +231,26 @@ cudaError_t launch_autos(const Shape& s, const uint8_t* d_in, int T_blk, long lo
   if (T_blk == 0) return cudaSuccess;
   dim3 grid((s.N + 31) / 32, s.C);
   autos_kernel<<<grid, AW * 32, 0, st>>>(d_in, s.N, s.C, T_blk, d_autos, d_soff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dump_select(long long* d_acc, const int* d_st, int n_st, int f0, int nf, void* d_out, int fmt,
+                               long long n_samples, int reset, const Shape2& g, cudaStream_t st) {
+  const long long units = (long long)nf * (g.autos ? (long long)n_st * g.npol : (long long)n_st * (n_st + 1) / 2 * g.P);
+  if (units == 0) return cudaSuccess;
+  long long blocks = (units + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  dump_select_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, d_st, n_st, f0, nf, d_out, fmt, n_samples, reset, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_base(long long* d_base, const int* d_st, int n_st, long long value, const Shape2& g,
+                            cudaStream_t st) {
+  const long long n = g.autos ? (long long)n_st * g.npol : (long long)n_st * (n_st + 1) / 2;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks == 0) return cudaSuccess;
+  set_base_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_base, d_st, n_st, value, g.npol, g.autos);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ Layout make_layout(int N, int C, int T, int npol) {
   L.s.S = N / npol;
   L.s.Bs = (long long)L.s.S * (L.s.S + 1) / 2;
   L.s.P = npol * npol;
+  if (L.s.Bs * L.s.P >= (1LL << 31)) return L;  // cells per channel are indexed with 32-bit integers
   unsigned long long x;
   if (!mul_ok((unsigned long long)C, (unsigned long long)L.s.Bs * L.s.P * 2, &x) || x > (1ull << 58)) return L;
   L.cross_elems = (long long)x;
@@ -152,6 +153,11 @@ struct corr_ctx {
   int next_in;
   long long n_cross;
   long long n_auto;
+  // selective dumps: station list scratch and the per-cell sample counts at the last selective reset
+  int* d_sel;
+  int sel_cap;
+  long long* d_cross_base;  // [B_s], allocated at the first selective cross reset
+  long long* d_auto_base;   // [N], allocated at the first selective autos reset
 };
 
 namespace {
@@ -219,6 +225,9 @@ void free_ctx(corr_ctx* c) {
   cudaFree(c->d_stage[1]);
   cudaFree(c->d_in_stage[0]);
   cudaFree(c->d_in_stage[1]);
+  cudaFree(c->d_sel);
+  cudaFree(c->d_cross_base);
+  cudaFree(c->d_auto_base);
   for (int k = 0; k < 2; ++k) {
     if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
     if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
@@ -392,8 +401,8 @@ size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int
 corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol) {
   const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
   if (!L.ok) {
-    fail(CORR_ERR_ARG, "corr_create: invalid shape (need 1 <= N <= 2^20, 1 <= C <= 65535, T >= 1, n_pol in {1,2}, "
-                       "N % n_pol == 0, sizes within range)");
+    fail(CORR_ERR_ARG, "corr_create: invalid shape (need N >= 1, B_s n_pol^2 < 2^31, 1 <= C <= 65535, T >= 1, "
+                       "n_pol in {1,2}, N % n_pol == 0, sizes within range)");
     return nullptr;
   }
   int dev = 0;
@@ -575,6 +584,7 @@ int corr_reset(corr_ctx* c, int what, void* stream) {
   if (what & CORR_WHAT_CROSS) {
     cudaError_t e = cudaMemsetAsync(c->d_cross, 0, (size_t)c->L.cross_elems * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_soff, 0, (size_t)c->L.autos_elems * 16, st);
+    if (e == cudaSuccess && c->d_cross_base) e = cudaMemsetAsync(c->d_cross_base, 0, (size_t)c->L.s.Bs * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "corr_reset");
     c->n_cross = 0;
     c->n_off = 0;
@@ -582,6 +592,7 @@ int corr_reset(corr_ctx* c, int what, void* stream) {
   if (what & CORR_WHAT_AUTO) {
     cudaError_t e = cudaMemsetAsync(c->d_autos, 0, (size_t)c->L.autos_elems * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_soff_auto, 0, (size_t)c->L.autos_elems * 16, st);
+    if (e == cudaSuccess && c->d_auto_base) e = cudaMemsetAsync(c->d_auto_base, 0, (size_t)c->L.s.N * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "corr_reset");
     c->n_auto = 0;
     c->n_off_auto = 0;
@@ -608,6 +619,7 @@ int corr_dump(corr_ctx* c, void* out, int is_device_ptr, int what, int fmt, int 
   g.soff = what == CORR_WHAT_CROSS ? c->d_soff : c->d_soff_auto;
   g.t_off = what == CORR_WHAT_CROSS ? c->n_off : c->n_off_auto;
   g.autos = what == CORR_WHAT_AUTO ? 1 : 0;
+  g.base = what == CORR_WHAT_CROSS ? c->d_cross_base : c->d_auto_base;
   cudaError_t e;
   if (is_device_ptr) {
     const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
@@ -630,6 +642,93 @@ int corr_dump(corr_ctx* c, void* out, int is_device_ptr, int what, int fmt, int 
     }
   }
   if (reset) return corr_reset(c, what, stream);
+  return CORR_OK;
+}
+
+int corr_dump_stations(corr_ctx* c, const int* stations, int n_stations, void* out, int is_device_ptr, int what,
+                       int fmt, int reset, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_dump_stations: NULL context");
+  if (!out || !stations) return fail(CORR_ERR_ARG, "corr_dump_stations: NULL output or station list");
+  if (what != CORR_WHAT_CROSS && what != CORR_WHAT_AUTO)
+    return fail(CORR_ERR_ARG, "corr_dump_stations: what must be CROSS or AUTO");
+  if (fmt != CORR_FMT_CI64 && fmt != CORR_FMT_CF32 && fmt != CORR_FMT_CF32_NORM)
+    return fail(CORR_ERR_ARG, "corr_dump_stations: unknown format");
+  const int S = c->L.s.S;
+  if (n_stations < 1 || n_stations > S) return fail(CORR_ERR_ARG, "corr_dump_stations: need 1..S stations");
+  std::vector<char> seen((size_t)S, 0);
+  for (int k = 0; k < n_stations; ++k) {
+    const int a = stations[k];
+    if (a < 0 || a >= S) return fail(CORR_ERR_ARG, "corr_dump_stations: station " + std::to_string(a) + " out of range");
+    if (seen[(size_t)a]) return fail(CORR_ERR_ARG, "corr_dump_stations: station " + std::to_string(a) + " listed twice");
+    seen[(size_t)a] = 1;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n_stations > c->sel_cap) {
+    int* d = nullptr;
+    if (cudaMalloc(&d, (size_t)n_stations * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CORR_ERR_OOM, "corr_dump_stations: station list allocation");
+    }
+    cudaStreamSynchronize(st);  // the old list may still be read by queued work on this stream
+    cudaFree(c->d_sel);
+    c->d_sel = d;
+    c->sel_cap = n_stations;
+  }
+  long long** base = what == CORR_WHAT_CROSS ? &c->d_cross_base : &c->d_auto_base;
+  const size_t base_bytes = (size_t)(what == CORR_WHAT_CROSS ? c->L.s.Bs : c->L.s.N) * 8;
+  if (reset && !*base) {
+    if (cudaMalloc(base, base_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *base = nullptr;
+      return fail(CORR_ERR_OOM, "corr_dump_stations: sample-count allocation");
+    }
+    e = cudaMemsetAsync(*base, 0, base_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_dump_stations: sample-count init");
+  }
+  // pageable source: the call returns once the list has been staged, so `stations` may be reused
+  e = cudaMemcpyAsync(c->d_sel, stations, (size_t)n_stations * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_dump_stations: station list upload");
+  Shape2 g;
+  g.N = c->L.s.N;
+  g.npol = c->L.s.npol;
+  g.P = c->L.s.P;
+  g.Bs = c->L.s.Bs;
+  g.soff = what == CORR_WHAT_CROSS ? c->d_soff : c->d_soff_auto;
+  g.t_off = what == CORR_WHAT_CROSS ? c->n_off : c->n_off_auto;
+  g.autos = what == CORR_WHAT_AUTO ? 1 : 0;
+  g.base = *base;
+  long long* acc = what == CORR_WHAT_CROSS ? c->d_cross : c->d_autos;
+  const long long ns = what == CORR_WHAT_CROSS ? c->n_cross : c->n_auto;
+  const size_t esz = fmt == CORR_FMT_CI64 ? 8 : 4;
+  const size_t per_chan = (size_t)(what == CORR_WHAT_CROSS ? (long long)n_stations * (n_stations + 1) / 2 * g.P * 2
+                                                           : (long long)n_stations * g.npol) * esz;
+  const int C = c->L.s.C;
+  if (is_device_ptr) {
+    const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
+    e = launch_dump_select(acc, c->d_sel, n_stations, 0, C, out, fmt, ns, reset, g, st);
+    timer_end(c, CORR_KERNEL_DUMP, st, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_dump_stations: launch");
+  } else {
+    const int nf_chunk = (int)(kStageBytes / per_chan);
+    if (nf_chunk < 1) return fail(CORR_ERR_ARG, "corr_dump_stations: one channel exceeds the host staging buffer");
+    int buf = 0;
+    for (int f0 = 0; f0 < C; f0 += nf_chunk) {
+      const int nf = C - f0 < nf_chunk ? C - f0 : nf_chunk;
+      const bool tb = timer_begin(c, CORR_KERNEL_DUMP, st);
+      e = launch_dump_select(acc, c->d_sel, n_stations, f0, nf, c->d_stage[buf], fmt, ns, reset, g, st);
+      timer_end(c, CORR_KERNEL_DUMP, st, tb);
+      if (e != cudaSuccess) return cuda_fail(e, "corr_dump_stations: launch");
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + (size_t)f0 * per_chan, c->d_stage[buf], (size_t)nf * per_chan,
+                          cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return cuda_fail(e, "corr_dump_stations: copy");
+      buf ^= 1;
+    }
+  }
+  if (reset) {
+    e = launch_set_base(*base, c->d_sel, n_stations, ns, g, st);
+    if (e != cudaSuccess) return cuda_fail(e, "corr_dump_stations: sample-count update");
+  }
   return CORR_OK;
 }
 

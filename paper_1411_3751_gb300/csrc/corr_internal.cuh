@@ -38,6 +38,8 @@ struct Shape2 {
   const long long* soff;  // [C][N][2] offset sums of the tensor path
   long long t_off;        // samples accumulated through the tensor path
   int autos;              // 1: the accumulator is autos[C][N], else cross[C][B_s][P][2]
+  const long long* base;  // per station pair (cross) or input (autos): sample count at the cell's last
+                          // selective reset, or nullptr if no cell was ever reset selectively
 };
 
 // FP8 path tile: c-side block of 64 inputs (128 operand rows, the MMA's M), a-side block starting
@@ -122,6 +124,13 @@ size_t f8_smem_bytes();
 
 // Dump elements [k_base, k_base + n_elems) of an accumulator, corrected with g (cross dumps: k_base
 // and n_elems even, i.e. whole (re, im) cells).
+// Selective dump of the cells among stations st[0..n_st) for channels [f0, f0 + nf) (output indexed from
+// channel f0); with reset, each dumped cell is set so that its corrected value restarts from zero.
+cudaError_t launch_dump_select(long long* d_acc, const int* d_st, int n_st, int f0, int nf, void* d_out, int fmt,
+                               long long n_samples, int reset, const Shape2& g, cudaStream_t st);
+// base[b] (cross: station pairs among st) or base[i] (autos: inputs of st) = value.
+cudaError_t launch_set_base(long long* d_base, const int* d_st, int n_st, long long value, const Shape2& g,
+                            cudaStream_t st);
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
                         long long k_base, const Shape2& g, cudaStream_t st);
 

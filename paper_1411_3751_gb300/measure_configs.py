@@ -7,9 +7,11 @@
 * group: sub-arrays of 32, 64, 200, 256 and 512 inputs with 2400, 600, 300, 150 and 109 channels of
   4096 samples: one autotuned grouped launch replayed from a CUDA graph vs separate per-array launches;
 * stream: one 512-input x 2400-channel stream and three 64-input streams in 10 ms blocks with 9 s
-  cross-power and 1 s total-power dumps over >= 100 s-equivalent; real-time factor and dump latency.
+  cross-power and 1 s total-power dumps over >= 100 s-equivalent; real-time factor and dump latency;
+* fastdump: the 512-input x 2400-channel stream at the paper's minimum dump time (0.33 s = 8000
+  samples, float32 visibilities) with 1 s total power of ten outrigger stations (selective dumps).
 
-    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream]
+    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream|fastdump]
 """
 from __future__ import annotations
 
@@ -94,6 +96,24 @@ def stream_loop(corr, synth, torch, n_blocks=10000):
     return out
 
 
+def fast_dump(corr, synth, torch, n_blocks=60):
+    from . import stream
+
+    outr = (251, 252, 253, 254, 255, 3, 77, 128, 200, 9)
+    sp = stream.StreamSpec("leda512_fast", 512, 2400, block_samples=8000, gulp_blocks=1, cross_every=1,
+                           auto_every=3, seed=0x14113751 + 6, outriggers=outr, cross_fmt=corr.CORR_FMT_CF32)
+    srv = stream.Server(hbm_budget_bytes=sp.footprint() + (1 << 30), keep_dumps=0)
+    try:
+        srv.admit(sp)
+        out = srv.run(n_blocks)
+    finally:
+        srv.close()
+    out["config"] = ("fastdump: 512 x 2400 inputs x channels, 8000-sample blocks (0.33 s), float32 cross dump "
+                     "every block, outrigger total power every 3 blocks, %d blocks" % n_blocks)
+    out["cross_bytes_per_dump"] = 2400 * 32896 * 4 * 2 * 4
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="")
@@ -109,12 +129,14 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
-    todo = [a.only] if a.only else ["precision", "group", "stream"]
+    todo = [a.only] if a.only else ["precision", "group", "stream", "fastdump"]
     for name in todo:
         if name == "precision":
             r = precision(corr, synth, torch)
         elif name == "group":
             r = group(corr, synth, torch)
+        elif name == "fastdump":
+            r = fast_dump(corr, synth, torch)
         else:
             r = stream_loop(corr, synth, torch, a.stream_blocks)
         print(json.dumps({"measure": name, **r}))

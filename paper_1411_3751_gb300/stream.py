@@ -9,6 +9,11 @@ F-engine data are not available) one gulp of `gulp_blocks` blocks at a time; eac
 events from the moment the last block of its window has been generated to the moment its host copy
 is complete. The real-time factor is reported for the whole loop (the input generator shares the GPU)
 and for the correlator's own work (accumulate and dump calls, timed with events).
+
+With `outriggers` set, the total-power dump covers only those stations (selective dump and reset of
+their cells, Sec. 2.6); the cross dump then carries the full visibilities. `cross_fmt` selects the
+cross dump format (CF32 is exact while a dump's sums stay below 2^24, e.g. the paper's 0.33 s
+minimum dump time of Table 1: 8000 samples x 128 < 2^24).
 """
 from __future__ import annotations
 
@@ -32,6 +37,8 @@ class StreamSpec:
     auto_every: int = 100        # blocks per total-power dump (1 s)
     seed: int = 0x14113751 + 5
     kind: str = "gauss_tone"
+    outriggers: tuple = ()       # stations whose total power alone is dumped at the auto cadence (Sec. 2.6)
+    cross_fmt: int = corr.CORR_FMT_CI64
 
     def gulp_samples(self) -> int:
         return self.block_samples * self.gulp_blocks
@@ -81,8 +88,11 @@ class Server:
             return False
         xc = corr.Correlator(spec.n_inputs, spec.n_chans, spec.gulp_samples(), spec.n_pol, path="fp8tc")
         buf = torch.empty((spec.gulp_samples(), spec.n_chans, spec.n_inputs), dtype=torch.uint8, device="cuda")
-        cross_h = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64).pin_memory()
-        autos_h = torch.empty(xc.out_shape(corr.CORR_WHAT_AUTO), dtype=torch.int64).pin_memory()
+        cdt = torch.int64 if spec.cross_fmt == corr.CORR_FMT_CI64 else torch.float32
+        cross_h = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=cdt).pin_memory()
+        ashape = (xc.station_out_shape(corr.CORR_WHAT_AUTO, len(spec.outriggers)) if spec.outriggers
+                  else xc.out_shape(corr.CORR_WHAT_AUTO))
+        autos_h = torch.empty(ashape, dtype=torch.int64).pin_memory()
         self.streams.append(_Live(spec, xc, buf, cross_h, autos_h))
         self.used += fp
         return True
@@ -119,7 +129,12 @@ class Server:
                 for kind, every, what, host in (("auto", sp.auto_every, corr.CORR_WHAT_AUTO, live.autos_host),
                                                 ("cross", sp.cross_every, corr.CORR_WHAT_CROSS, live.cross_host)):
                     if live.blocks_done % every == 0:
-                        live.xc.dump(what, reset=True, out=host)
+                        if kind == "auto" and sp.outriggers:
+                            live.xc.dump_stations(sp.outriggers, what, reset=True, out=host)
+                        elif kind == "cross":
+                            live.xc.dump(what, fmt=sp.cross_fmt, reset=True, out=host)
+                        else:
+                            live.xc.dump(what, reset=True, out=host)
                         done = ev()
                         done.record()
                         pending.append((live, kind, ready, done))

@@ -63,7 +63,7 @@ def test_host_only_helpers(lib):
 
 
 @pytest.mark.parametrize("args", [(0, 1, 1, 1), (4, 0, 1, 2), (4, 1, 0, 2), (5, 1, 1, 2), (4, 1, 1, 3), (-2, 1, 1, 1),
-                                  (4, 65536, 1, 2), ((1 << 20) + 2, 1, 1, 2)])
+                                  (4, 65536, 1, 2), (65536, 1, 1, 2)])
 def test_create_rejects_bad_shapes(lib, args):
     with pytest.raises(lib.CorrError) as ei:
         lib.corr_create(*args)

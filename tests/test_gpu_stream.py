@@ -72,3 +72,40 @@ def test_stream_loop_512_plus_three_64(env):
                         assert tuple(cross[f, b, pq]) == tuple(got[k]), (sp.name, f, b, pq)
     finally:
         srv.close()
+
+
+def test_fast_dump_mode_with_outriggers(env):
+    """The paper's minimum dump time (0.33 s = one 8000-sample group, Table 1) with float32 visibilities
+    (exact at this length) and 1 s total power of ten outrigger stations by selective dumps (Sec. 2.6)."""
+    corr, stream, synth, torch = env
+    outr = (251, 252, 253, 254, 255, 3, 77, 128, 200, 9)
+    sp = stream.StreamSpec("fast512", 512, 240, block_samples=8000, gulp_blocks=1, cross_every=1, auto_every=3,
+                           seed=0x14113751 + 6, outriggers=outr, cross_fmt=corr.CORR_FMT_CF32)
+    srv = stream.Server(hbm_budget_bytes=sp.footprint() + (1 << 30), keep_dumps=2)
+    try:
+        assert srv.admit(sp)
+        out = srv.run(6)
+        st = out["streams"]["fast512"]
+        assert st["cross_dumps"] == 6 and st["auto_dumps"] == 2
+        live = srv.streams[0]
+        gen = synth.Spec(kind=sp.kind, seed=sp.seed)
+        rng = np.random.default_rng(66)
+        for (b0, cross) in live.cross_dumps:
+            assert cross.dtype == np.float32
+            for f in (5, 239):
+                hf = synth.generate_host(gen, 8000, sp.n_chans, sp.n_inputs, t0=b0 * 8000, c_range=(f, f + 1))
+                cells, idx = [], []
+                for _ in range(32):
+                    sa = int(rng.integers(0, 256))
+                    sc = int(rng.integers(0, sa + 1))
+                    p, q = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+                    cells.append((0, 2 * sa + p, 2 * sc + q))
+                    idx.append((sa * (sa + 1) // 2 + sc, 2 * p + q))
+                got = oracle.cells(hf, cells).astype(np.float32)
+                for k, (b, pq) in enumerate(idx):
+                    assert tuple(cross[f, b, pq]) == tuple(got[k]), (b0, f, b, pq)
+        for (b0, autos) in live.auto_dumps:
+            hf = synth.generate_host(gen, 3 * 8000, sp.n_chans, sp.n_inputs, t0=b0 * 8000)
+            assert np.array_equal(autos, oracle.station_autos(hf, outr, 2)), b0
+    finally:
+        srv.close()

@@ -270,3 +270,35 @@ def test_pack_unpack_roundtrip_and_range():
     assert oracle.pack(np.array([-8]), np.array([7]))[0] == 0x87
     with pytest.raises(ValueError):
         oracle.pack(np.array([8]), np.array([0]))
+
+
+@pytest.mark.parametrize("n_pol", [1, 2])
+def test_station_subset_brute_force(n_pol):
+    """Selected-station cells (Sec. 2.6) against the brute-force Hermitian matrix, for an unordered
+    station list: element (k, l, p, q) = V[st[k] p, st[l] q], conjugated storage when st[k] < st[l]."""
+    rng = np.random.default_rng(31 + n_pol)
+    T, C, S = 57, 3, 6
+    s = _rand_bytes(rng, T, C, S * n_pol)
+    fr, fi = _brute_full(s)
+    st = [4, 1, 5, 0]
+    got = oracle.station_cross(s, st, n_pol)
+    for k in range(len(st)):
+        for l in range(k + 1):
+            for p in range(n_pol):
+                for q in range(n_pol):
+                    i, j = st[k] * n_pol + p, st[l] * n_pol + q
+                    e = got[:, k * (k + 1) // 2 + l, p * n_pol + q]
+                    np.testing.assert_array_equal(e[:, 0], fr[:, i, j])
+                    np.testing.assert_array_equal(e[:, 1], fi[:, i, j])
+    ga = oracle.station_autos(s, st, n_pol)
+    for k, a in enumerate(st):
+        for p in range(n_pol):
+            np.testing.assert_array_equal(ga[:, k, p], np.einsum("cnn->cn", fr)[:, a * n_pol + p])
+
+
+def test_station_subset_of_all_stations_is_the_full_dump():
+    rng = np.random.default_rng(77)
+    s = _rand_bytes(rng, 40, 2, 10)
+    cross, autos = oracle.correlate(s, 2)
+    np.testing.assert_array_equal(oracle.station_cross(s, range(5), 2), cross)
+    np.testing.assert_array_equal(oracle.station_autos(s, range(5), 2).reshape(2, 10), autos)

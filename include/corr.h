@@ -173,6 +173,29 @@ int corr_dump(corr_ctx* ctx, void* out, int is_device_ptr, int what, int fmt, in
 int corr_dump_stations(corr_ctx* ctx, const int* stations, int n_stations, void* out, int is_device_ptr, int what,
                        int fmt, int reset, void* cuda_stream);
 
+/* Input sample types of corr_requantize. */
+typedef enum corr_in_type { CORR_IN_CI32 = 0 /* int32 re, im (e.g. 18+18-bit PFB output) */,
+                            CORR_IN_CF32 = 1 /* float32 re, im */ } corr_in_type;
+
+/*
+ * corr_requantize - the F-engine tail in front of the X-engine (Sec. 2.2): the PFB output is scaled
+ * by a digital gain, requantised from 18+18 bits to 4+4 bits, reduced to a contiguous range of
+ * channels and corner-turned so that inputs are grouped by channel (the layout corr_accumulate reads).
+ *   d_in   device, [n_inputs][n_time][n_pfb_chans] complex samples of `in_type` (8 bytes each);
+ *   d_out  device, uint8 [n_time][n_chans][n_inputs], byte = (Re << 4) | (Im & 0xF) (caller-owned);
+ *   chan0, n_chans  the selected channels chan0 .. chan0 + n_chans - 1 of the PFB;
+ *   gain / d_gains  one factor across the band (the paper's scheme), or, if d_gains is not NULL, a
+ *                   device array of n_chans per-channel factors (the per-channel refinement it
+ *                   mentions);
+ *   symmetric       clip to [-7, 7] instead of the full two's-complement range [-8, 7].
+ * Per component v: x = fl32(gain * (float)v) (one IEEE single-precision product), q = round-to-nearest-
+ * even(x) clipped to the range; NaN gives 0. The paper does not state the rounding rule; this is the
+ * reading taken. Asynchronous on cuda_stream. CORR_ERR_ARG for NULL buffers, d_in not 8-byte aligned,
+ * an unknown type, a NaN gain, or a channel range outside the PFB or above 65535 channels.
+ */
+int corr_requantize(const void* d_in, int in_type, int n_inputs, int n_time, int n_pfb_chans, int chan0, int n_chans,
+                    float gain, const float* d_gains, int symmetric, void* d_out, void* cuda_stream);
+
 /* Samples per channel accumulated into `what` since creation or its last reset (host-side count). */
 long long corr_samples_accumulated(const corr_ctx* ctx, int what);
 

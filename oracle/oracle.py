@@ -17,6 +17,14 @@ Sec. 2.6, the auto-correlation cells; Sec. 2.2, samples requantised to 4+4 bits)
   sum_t x_{st[k] p}(t) conj(x_{st[l] q}(t))`` for list positions k >= l, and
   ``station_autos[f, k, p] = autos[f, st[k] n_pol + p]``.
 
+Requantiser (the F-engine tail, Sec. 2.2: a digital gain across the band, requantisation from 18+18
+to 4+4 bits, channel selection, corner turn; the rounding rule is not stated, the reading taken is
+round to nearest, ties to even, in IEEE single precision):
+
+* per component v: ``x = fl32(gain * fl32(v))``, ``q = clip(rint(x), lo, 7)``, lo = -8 (or -7 when
+  symmetric), NaN -> 0;
+* ``out[t, c, n] = (q_re << 4) | (q_im & 0xF)`` for PFB channel chan0 + c of input n at time t.
+
 Dump formats (the paper stores visibilities as 32-bit floats after averaging, Sec. 2.5; the
 integer sum is the exact product, so two float views are defined on top of it):
 
@@ -148,6 +156,29 @@ def station_autos(samples: np.ndarray, stations, n_pol: int) -> np.ndarray:
     a = autos(samples)
     idx = [int(s) * n_pol + p for s in stations for p in range(n_pol)]
     return a[:, idx].reshape(a.shape[0], len(stations), n_pol)
+
+
+def requantize(x: np.ndarray, chan0: int, n_chans: int, gain: float = 1.0, gains=None,
+               symmetric: bool = False) -> np.ndarray:
+    """PFB output ``x[N][T][F][2]`` (int32 or float32) -> packed 4+4-bit ``uint8[T][n_chans][N]``."""
+    x = np.asarray(x)
+    if x.ndim != 4 or x.shape[3] != 2 or x.dtype not in (np.int32, np.float32):
+        raise ValueError("x must be [N][T][F][2] int32 or float32")
+    # 1) channel selection
+    sel = x[:, :, chan0:chan0 + n_chans, :]
+    if sel.shape[2] != n_chans:
+        raise ValueError("channel range outside the PFB")
+    # 2) digital gain: one IEEE single-precision product per component
+    g = np.float32(gain) if gains is None else np.asarray(gains, dtype=np.float32)[None, None, :, None]
+    with np.errstate(invalid="ignore", over="ignore"):
+        xf = (sel.astype(np.float32) * g).astype(np.float32)
+    # 3) round to nearest, ties to even; 4) clip; NaN -> 0
+    r = np.rint(xf)
+    lo = -7.0 if symmetric else -8.0
+    r = np.where(np.isnan(r), 0.0, np.clip(r, lo, 7.0)).astype(np.int64)
+    # 5) pack Re in the high nibble; 6) corner turn [N][T][C] -> [T][C][N]
+    packed = (((r[..., 0] & 0xF) << 4) | (r[..., 1] & 0xF)).astype(np.uint8)
+    return np.ascontiguousarray(packed.transpose(1, 2, 0))
 
 
 def to_format(values: np.ndarray, fmt: int, n_samples: int) -> np.ndarray:

@@ -36,6 +36,8 @@ SIGNATURES = [
     ("corr_accumulate_autos", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_dump", _c_int, [_c_vp, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
     ("corr_dump_stations", _c_int, [_c_vp, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
+    ("corr_requantize", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.c_float, _c_vp,
+                                 _c_int, _c_vp, _c_vp]),
     ("corr_samples_accumulated", _c_ll, [_c_vp, _c_int]),
     ("corr_reset", _c_int, [_c_vp, _c_int, _c_vp]),
     ("corr_sync", _c_int, [_c_vp, _c_vp]),
@@ -124,6 +126,39 @@ def corr_accumulate_autos(ctx: int, d_samples: int, stream: int) -> int:
 
 def corr_dump(ctx: int, out: int, is_device_ptr: int, what: int, fmt: int, reset: int, stream: int) -> int:
     return _check(_lib.corr_dump(ctx, out, is_device_ptr, what, fmt, reset, stream), "corr_dump")
+
+
+CORR_IN_CI32, CORR_IN_CF32 = 0, 1
+
+
+def corr_requantize(d_in: int, in_type: int, n_inputs: int, n_time: int, n_pfb_chans: int, chan0: int, n_chans: int,
+                    gain: float, d_gains: int, symmetric: int, d_out: int, stream: int) -> int:
+    return _check(_lib.corr_requantize(d_in, in_type, n_inputs, n_time, n_pfb_chans, chan0, n_chans, gain, d_gains,
+                                       symmetric, d_out, stream), "corr_requantize")
+
+
+def requantize(x, chan0: int, n_chans: int, gain: float = 1.0, gains=None, symmetric: bool = False, out=None,
+               stream=None):
+    """torch wrapper: x is a cuda tensor [N][T][F][2] of int32 or float32; returns uint8 [T][n_chans][N]."""
+    import torch
+
+    if not x.is_cuda or x.dim() != 4 or x.shape[3] != 2 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous cuda tensor [N][T][F][2]")
+    if x.dtype == torch.int32:
+        in_type = CORR_IN_CI32
+    elif x.dtype == torch.float32:
+        in_type = CORR_IN_CF32
+    else:
+        raise ValueError("x must be int32 or float32")
+    N, T, F = x.shape[0], x.shape[1], x.shape[2]
+    if out is None:
+        out = torch.empty((T, n_chans, N), dtype=torch.uint8, device=x.device)
+    if gains is not None and (not gains.is_cuda or gains.dtype != torch.float32 or gains.numel() != n_chans):
+        raise ValueError("gains must be a cuda float32 tensor of n_chans values")
+    corr_requantize(x.data_ptr(), in_type, N, T, F, chan0, n_chans, float(gain),
+                    gains.data_ptr() if gains is not None else None, 1 if symmetric else 0, out.data_ptr(),
+                    _stream_handle(stream))
+    return out
 
 
 def corr_dump_stations(ctx: int, stations, n_stations: int, out: int, is_device_ptr: int, what: int, fmt: int,

@@ -732,6 +732,23 @@ int corr_dump_stations(corr_ctx* c, const int* stations, int n_stations, void* o
   return CORR_OK;
 }
 
+int corr_requantize(const void* d_in, int in_type, int n_inputs, int n_time, int n_pfb_chans, int chan0, int n_chans,
+                    float gain, const float* d_gains, int symmetric, void* d_out, void* stream) {
+  if (!d_in || !d_out) return fail(CORR_ERR_ARG, "corr_requantize: NULL buffer");
+  if (in_type != CORR_IN_CI32 && in_type != CORR_IN_CF32) return fail(CORR_ERR_ARG, "corr_requantize: unknown input type");
+  if ((reinterpret_cast<uintptr_t>(d_in) & 7) != 0 || (d_gains && (reinterpret_cast<uintptr_t>(d_gains) & 3) != 0))
+    return fail(CORR_ERR_ARG, "corr_requantize: samples must be 8-byte and gains 4-byte aligned");
+  if (n_inputs < 1 || n_time < 0 || n_pfb_chans < 1 || n_chans < 1 || chan0 < 0 || n_chans > 65535 ||
+      (long long)chan0 + n_chans > n_pfb_chans)
+    return fail(CORR_ERR_ARG, "corr_requantize: need 0 <= chan0, chan0 + n_chans <= n_pfb_chans, n_chans <= 65535");
+  if (!(gain == gain)) return fail(CORR_ERR_ARG, "corr_requantize: gain is NaN");
+  const cudaError_t e = launch_requant(d_in, in_type == CORR_IN_CI32 ? 0 : 1, n_inputs, n_time, n_pfb_chans, chan0,
+                                       n_chans, gain, d_gains, symmetric != 0, static_cast<uint8_t*>(d_out),
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_requantize: launch");
+  return CORR_OK;
+}
+
 long long corr_samples_accumulated(const corr_ctx* c, int what) {
   if (!c) return CORR_ERR_ARG;
   if (what == CORR_WHAT_CROSS) return c->n_cross;

@@ -131,6 +131,9 @@ cudaError_t launch_dump_select(long long* d_acc, const int* d_st, int n_st, int 
 // base[b] (cross: station pairs among st) or base[i] (autos: inputs of st) = value.
 cudaError_t launch_set_base(long long* d_base, const int* d_st, int n_st, long long value, const Shape2& g,
                             cudaStream_t st);
+// F-engine tail: gain, round, clip to 4+4 bits, channel selection and corner turn (requant.cu).
+cudaError_t launch_requant(const void* d_in, int in_type, int N, int T, int F, int chan0, int C, float gain,
+                           const float* d_gains, int symmetric, uint8_t* d_out, cudaStream_t st);
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
                         long long k_base, const Shape2& g, cudaStream_t st);
 

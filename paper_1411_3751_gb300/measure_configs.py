@@ -8,10 +8,13 @@
   4096 samples: one autotuned grouped launch replayed from a CUDA graph vs separate per-array launches;
 * stream: one 512-input x 2400-channel stream and three 64-input streams in 10 ms blocks with 9 s
   cross-power and 1 s total-power dumps over >= 100 s-equivalent; real-time factor and dump latency;
+* requant: the F-engine tail at the paper's sizes: 512 inputs x 1024 spectra of a 4096-channel PFB
+  (18+18-bit integers), 2398 channels selected, requantised to 4+4 bits and corner-turned; bytes moved
+  per second against the measured HBM copy bandwidth;
 * fastdump: the 512-input x 2400-channel stream at the paper's minimum dump time (0.33 s = 8000
   samples, float32 visibilities) with 1 s total power of ten outrigger stations (selective dumps).
 
-    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream|fastdump]
+    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream|fastdump|requant]
 """
 from __future__ import annotations
 
@@ -114,6 +117,38 @@ def fast_dump(corr, synth, torch, n_blocks=60):
     return out
 
 
+def requant(corr, synth, torch, reps=5):
+    import json as _json
+
+    N, T, F, chan0, C = 512, 1024, 4096, 1229, 2398
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0x14113751 + 7)
+    x = (torch.randn((N, T, F, 2), device="cuda", generator=g) * 3000.0).round_().clamp_(-(1 << 17), (1 << 17) - 1)
+    x = x.to(torch.int32)
+    out = torch.empty((T, C, N), dtype=torch.uint8, device="cuda")
+    gain = 2.5 / 3000.0
+    corr.requantize(x, chan0, C, gain=gain, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        corr.requantize(x, chan0, C, gain=gain, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    moved = N * T * C * (8 + 1)  # read the selected int32 pairs, write one byte per sample
+    try:
+        peaks = _json.load(open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                             "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+    except Exception:
+        hbm = 6800.0
+    return {"config": "requant: N=512, T=1024, F=4096, chan0=1229, C=2398, int32 in", "ms": ms,
+            "gbs": moved / (ms / 1e3) / 1e9, "frac_of_hbm": moved / (ms / 1e3) / 1e9 / hbm,
+            "samples_per_s": N * T * C / (ms / 1e3),
+            "real_time_factor": (T / 24000.0) / (ms / 1e3)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="")
@@ -129,7 +164,7 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
-    todo = [a.only] if a.only else ["precision", "group", "stream", "fastdump"]
+    todo = [a.only] if a.only else ["precision", "group", "stream", "fastdump", "requant"]
     for name in todo:
         if name == "precision":
             r = precision(corr, synth, torch)
@@ -137,6 +172,8 @@ def main(argv=None):
             r = group(corr, synth, torch)
         elif name == "fastdump":
             r = fast_dump(corr, synth, torch)
+        elif name == "requant":
+            r = requant(corr, synth, torch)
         else:
             r = stream_loop(corr, synth, torch, a.stream_blocks)
         print(json.dumps({"measure": name, **r}))

@@ -1,6 +1,7 @@
 """Profiling driver: a few accumulate calls on one synthetic workload, for `ncu -k <kernel> -s/-c`.
 
     python -m paper_1411_3751_gb300.profile_case --n 512 --c 128 --t 8192 --blocks 3 --path fp8tc
+    python -m paper_1411_3751_gb300.profile_case --requant --n 512 --c 2398 --t 256 --blocks 3
 
 Holds a single input block on the device (the same block is accumulated --blocks times), so the
 device footprint stays at a few GB for the 512-input, 128-channel case.
@@ -21,6 +22,9 @@ def main(argv=None):
     ap.add_argument("--blocks", type=int, default=3)
     ap.add_argument("--path", default="fp8tc")
     ap.add_argument("--seed", type=int, default=0x14113751 + 2)
+    ap.add_argument("--requant", action="store_true",
+                    help="profile the requantiser instead: --n inputs x --t spectra of a 4096-channel PFB, "
+                         "--c channels selected (int32 input)")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -32,6 +36,16 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
+    if a.requant:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(a.seed)
+        pfb = (torch.randn((a.n, a.t, 4096, 2), device="cuda", generator=g) * 3000.0).round_().to(torch.int32)
+        out = torch.empty((a.t, a.c, a.n), dtype=torch.uint8, device="cuda")
+        for _ in range(a.blocks):
+            corr.requantize(pfb, 1229, a.c, gain=2.5 / 3000.0, out=out)
+        torch.cuda.synchronize()
+        print("profile_case ok: requant N=%d T=%d C=%d blocks=%d" % (a.n, a.t, a.c, a.blocks))
+        return
     x = synth.generate_device(synth.Spec(kind="gauss_tone", seed=a.seed), a.t, a.c, a.n)
     with corr.Correlator(a.n, a.c, a.t, a.npol, path=a.path) as xc:
         for _ in range(a.blocks):

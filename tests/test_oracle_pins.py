@@ -302,3 +302,58 @@ def test_station_subset_of_all_stations_is_the_full_dump():
     cross, autos = oracle.correlate(s, 2)
     np.testing.assert_array_equal(oracle.station_cross(s, range(5), 2), cross)
     np.testing.assert_array_equal(oracle.station_autos(s, range(5), 2).reshape(2, 10), autos)
+
+
+def _half_even_div(v: int, k: int) -> int:
+    """round(v / 2^k), ties to even, in exact integer arithmetic."""
+    q, r = divmod(v, 1 << k)
+    half = 1 << (k - 1)
+    if r > half or (r == half and q % 2 == 1):
+        q += 1
+    return q
+
+
+def test_requantize_power_of_two_gain_matches_integer_rounding():
+    """gain = 2^-k makes the float product exact: the result is integer round-half-even then clip."""
+    rng = np.random.default_rng(5)
+    N, T, F = 3, 4, 9
+    x = rng.integers(-(1 << 17), 1 << 17, size=(N, T, F, 2)).astype(np.int32)
+    x[0, 0, 0] = (3 << 12, -(5 << 12))   # exact ties +-1.5 / 2.5 at k = 13
+    x[0, 0, 1] = (1 << 12, -(1 << 12))   # +-0.5
+    got = oracle.requantize(x, chan0=2, n_chans=6, gain=2.0 ** -13)
+    for n in range(N):
+        for t in range(T):
+            for c in range(6):
+                q = [min(7, max(-8, _half_even_div(int(v), 13))) for v in x[n, t, 2 + c]]
+                assert got[t, c, n] == (((q[0] & 0xF) << 4) | (q[1] & 0xF))
+    assert oracle.requantize(x, 0, 2, 2.0 ** -13)[0, 0, 0] == (((2 & 0xF) << 4) | (-2 & 0xF))
+    assert oracle.requantize(x, 0, 2, 2.0 ** -13)[0, 1, 0] == 0x00
+
+
+def test_requantize_identity_clip_and_specials():
+    # integers already in range pass through unchanged with gain 1
+    v = np.arange(-8, 8, dtype=np.int32)
+    x = np.stack(np.meshgrid(v, v, indexing="ij"), axis=-1).reshape(1, 1, 256, 2)
+    got = oracle.requantize(x, 0, 256, 1.0)
+    np.testing.assert_array_equal(got[0, :, 0], oracle.pack(x[0, 0, :, 0], x[0, 0, :, 1]))
+    # clipping, the symmetric variant, NaN and infinities
+    f = np.array([[[[100.0, -100.0], [np.nan, np.inf], [-np.inf, 7.5], [-8.5, 6.5]]]], dtype=np.float32)
+    full = oracle.requantize(f, 0, 4, 1.0)[0, :, 0]
+    sym = oracle.requantize(f, 0, 4, 1.0, symmetric=True)[0, :, 0]
+    np.testing.assert_array_equal(full, [0x78, 0x07, 0x87, 0x86])  # (7,-8) (0,7) (-8,7: 7.5 -> 8 -> 7) (-8, 6)
+    np.testing.assert_array_equal(sym, [0x79, 0x07, 0x97, 0x96])
+
+
+def test_requantize_corner_turn_and_per_channel_gains():
+    rng = np.random.default_rng(8)
+    N, T, F = 5, 3, 11
+    x = (rng.standard_normal((N, T, F, 2)) * 3).astype(np.float32)
+    g = np.linspace(0.5, 2.0, 7).astype(np.float32)
+    got = oracle.requantize(x, 3, 7, gains=g)
+    for n in range(N):
+        for t in range(T):
+            for c in range(7):
+                q = [int(min(7, max(-8, np.rint(np.float32(g[c]) * x[n, t, 3 + c, k])))) for k in range(2)]
+                assert got[t, c, n] == (((q[0] & 0xF) << 4) | (q[1] & 0xF))
+    np.testing.assert_array_equal(oracle.requantize(x, 3, 7, gains=np.full(7, 1.25, np.float32)),
+                                  oracle.requantize(x, 3, 7, gain=1.25))

@@ -121,35 +121,21 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus):
-    import torch
+    from paper_1411_3751_gb300 import replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    return world, rank, local
+    return replicas.init("nccl")
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
+    from paper_1411_3751_gb300 import replicas
 
-        dist.barrier()
+    replicas.barrier(world)
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_1411_3751_gb300 import replicas
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return replicas.max_over_ranks(x, world, "cuda")
 
 
 def cpu_baseline(seconds_target=15.0):
@@ -400,10 +386,9 @@ def main():
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
+    from paper_1411_3751_gb300 import replicas
 
-        dist.destroy_process_group()
+    replicas.finalize(world)
     return 0
 
 

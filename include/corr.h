@@ -196,6 +196,32 @@ typedef enum corr_in_type { CORR_IN_CI32 = 0 /* int32 re, im (e.g. 18+18-bit PFB
 int corr_requantize(const void* d_in, int in_type, int n_inputs, int n_time, int n_pfb_chans, int chan0, int n_chans,
                     float gain, const float* d_gains, int symmetric, void* d_out, void* cuda_stream);
 
+/*
+ * corr_pfb_coeffs - the PFB prototype filter (Sec. 2.2: 4 taps, 8192 points, Hamming window, 18-bit
+ * coefficients) for n_taps x n_fft coefficients, written to the HOST array h_out[n_taps * n_fft]:
+ *   h[j] = floor(s w[j] sinc((j - (L - 1) / 2) / n_fft) + 1/2),  L = n_taps n_fft,
+ *   w[j] = 0.54 - 0.46 cos(2 pi j / (L - 1)),  sinc(u) = sin(pi u) / (pi u),
+ * with s chosen so that the largest |h| is 2^17 - 1. The window centring and the rounding are the
+ * readings taken where the paper is silent. CORR_ERR_ARG unless n_fft is a power of two and
+ * 1 <= n_taps <= 64.
+ */
+int corr_pfb_coeffs(int n_fft, int n_taps, int32_t* h_out);
+
+/*
+ * corr_pfb - polyphase filterbank F-engine on the device (Sec. 2.2), n_fft = 8192:
+ *   y_t[m] = sum_{p < n_taps} h[p 8192 + m] x[(t + p) 8192 + m]            (exact int32)
+ *   X_t[k] = 2^-13 sum_{m < 8192} y_t[m] exp(-2 pi i k m / 8192), k < 4096  (FP32 FFT)
+ * The paper's FFT halves at each of its 13 stages; the 2^-13 applies the same scale once.
+ *   d_adc     device int8 real samples, input n at d_adc + n * input_stride, n_samples valid each;
+ *   d_coeffs  device int32 [n_taps * 8192] (e.g. from corr_pfb_coeffs), 16-byte aligned;
+ *   d_out     device float32 complex [n_inputs][n_spectra][4096] (re, im): the CORR_IN_CF32 input
+ *             of corr_requantize.
+ * Spectrum t uses samples t * 8192 .. (t + n_taps) * 8192 - 1. Asynchronous on cuda_stream.
+ * CORR_ERR_ARG for NULL or misaligned buffers, or (n_spectra + n_taps - 1) * 8192 > n_samples.
+ */
+int corr_pfb(const int8_t* d_adc, int n_inputs, long long input_stride, long long n_samples, int n_taps,
+             const int32_t* d_coeffs, int n_spectra, void* d_out, void* cuda_stream);
+
 /* Samples per channel accumulated into `what` since creation or its last reset (host-side count). */
 long long corr_samples_accumulated(const corr_ctx* ctx, int what);
 

@@ -25,6 +25,16 @@ round to nearest, ties to even, in IEEE single precision):
   symmetric), NaN -> 0;
 * ``out[t, c, n] = (q_re << 4) | (q_im & 0xF)`` for PFB channel chan0 + c of input n at time t.
 
+PFB F-engine (Sec. 2.2: a 4-tap, 8192-point polyphase filterbank, FIR then FFT, Hamming window,
+18-bit coefficients, a halving at each FFT stage; window centring and coefficient rounding are the
+readings taken):
+
+* ``h[j] = floor(s w[j] sinc((j - (L - 1) / 2) / M) + 1/2)``, ``L = P M``, Hamming
+  ``w[j] = 0.54 - 0.46 cos(2 pi j / (L - 1))``, s such that max |h| = 2^17 - 1;
+* ``y_t[m] = sum_p h[p M + m] x[(t + p) M + m]`` (exact integers for 8-bit samples);
+* ``X_t[k] = M^-1 sum_m y_t[m] exp(-2 pi i k m / M)`` for k < M / 2 (the per-stage halving of a
+  radix-2 FFT over log2 M stages is a factor 1 / M in all).
+
 Dump formats (the paper stores visibilities as 32-bit floats after averaging, Sec. 2.5; the
 integer sum is the exact product, so two float views are defined on top of it):
 
@@ -179,6 +189,39 @@ def requantize(x: np.ndarray, chan0: int, n_chans: int, gain: float = 1.0, gains
     # 5) pack Re in the high nibble; 6) corner turn [N][T][C] -> [T][C][N]
     packed = (((r[..., 0] & 0xF) << 4) | (r[..., 1] & 0xF)).astype(np.uint8)
     return np.ascontiguousarray(packed.transpose(1, 2, 0))
+
+
+def pfb_coeffs(n_fft: int, n_taps: int) -> np.ndarray:
+    """Prototype filter ``h[n_taps * n_fft]`` (int64 values of 18-bit range)."""
+    L = n_fft * n_taps
+    j = np.arange(L, dtype=np.float64)
+    w = 0.54 - 0.46 * np.cos(2.0 * np.pi * j / (L - 1)) if L > 1 else np.ones(1)
+    h = w * np.sinc((j - 0.5 * (L - 1)) / n_fft)
+    s = 131071.0 / np.abs(h).max()
+    return np.floor(h * s + 0.5).astype(np.int64)
+
+
+def pfb_fir(adc: np.ndarray, n_fft: int, n_taps: int, coeffs=None) -> np.ndarray:
+    """FIR stage ``y[N][T][n_fft]`` of real samples ``adc[N][S]`` (int64 for integer input, else float64)."""
+    adc = np.asarray(adc)
+    h = pfb_coeffs(n_fft, n_taps) if coeffs is None else np.asarray(coeffs, dtype=np.int64)
+    N, S = adc.shape
+    T = S // n_fft - n_taps + 1
+    if T < 1:
+        raise ValueError("need at least n_taps frames")
+    integer = np.issubdtype(adc.dtype, np.integer)
+    frames = adc[:, :(T + n_taps - 1) * n_fft].reshape(N, T + n_taps - 1, n_fft)
+    frames = frames.astype(np.int64 if integer else np.float64)
+    y = np.zeros((N, T, n_fft), dtype=frames.dtype)
+    for p in range(n_taps):
+        y += frames[:, p:p + T, :] * h[p * n_fft:(p + 1) * n_fft][None, None, :]
+    return y
+
+
+def pfb(adc: np.ndarray, n_fft: int = 8192, n_taps: int = 4, coeffs=None) -> np.ndarray:
+    """PFB output ``X[N][T][n_fft / 2]`` complex128: FIR, then the real DFT scaled by 1 / n_fft."""
+    y = pfb_fir(adc, n_fft, n_taps, coeffs)
+    return np.fft.rfft(y.astype(np.float64), axis=-1)[..., :n_fft // 2] / n_fft
 
 
 def to_format(values: np.ndarray, fmt: int, n_samples: int) -> np.ndarray:

@@ -36,6 +36,8 @@ SIGNATURES = [
     ("corr_accumulate_autos", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_dump", _c_int, [_c_vp, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
     ("corr_dump_stations", _c_int, [_c_vp, _c_vp, _c_int, _c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp]),
+    ("corr_pfb_coeffs", _c_int, [_c_int, _c_int, _c_vp]),
+    ("corr_pfb", _c_int, [_c_vp, _c_int, ctypes.c_longlong, ctypes.c_longlong, _c_int, _c_vp, _c_int, _c_vp, _c_vp]),
     ("corr_requantize", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.c_float, _c_vp,
                                  _c_int, _c_vp, _c_vp]),
     ("corr_samples_accumulated", _c_ll, [_c_vp, _c_int]),
@@ -158,6 +160,49 @@ def requantize(x, chan0: int, n_chans: int, gain: float = 1.0, gains=None, symme
     corr_requantize(x.data_ptr(), in_type, N, T, F, chan0, n_chans, float(gain),
                     gains.data_ptr() if gains is not None else None, 1 if symmetric else 0, out.data_ptr(),
                     _stream_handle(stream))
+    return out
+
+
+def corr_pfb_coeffs(n_fft: int, n_taps: int):
+    """Prototype filter of the PFB as a numpy int32 array [n_taps * n_fft] (computed by the library)."""
+    import numpy as np
+
+    h = np.zeros(n_fft * n_taps, dtype=np.int32)
+    _check(_lib.corr_pfb_coeffs(n_fft, n_taps, h.ctypes.data), "corr_pfb_coeffs")
+    return h
+
+
+def corr_pfb(d_adc: int, n_inputs: int, input_stride: int, n_samples: int, n_taps: int, d_coeffs: int,
+             n_spectra: int, d_out: int, stream: int) -> int:
+    return _check(_lib.corr_pfb(d_adc, n_inputs, input_stride, n_samples, n_taps, d_coeffs, n_spectra, d_out, stream),
+                  "corr_pfb")
+
+
+PFB_FFT = 8192
+_pfb_coeff_cache = {}
+
+
+def pfb(adc, n_taps: int = 4, coeffs=None, out=None, stream=None):
+    """torch wrapper: adc is a cuda int8 tensor [N][S] of real samples; returns float32 [N][T][4096][2]
+    with T = S // 8192 - n_taps + 1 spectra (corr_pfb)."""
+    import torch
+
+    if not adc.is_cuda or adc.dtype != torch.int8 or adc.dim() != 2 or adc.stride(1) != 1:
+        raise ValueError("adc must be a cuda int8 tensor [N][S] with contiguous rows")
+    N, S = adc.shape
+    T = S // PFB_FFT - n_taps + 1
+    if T < 1:
+        raise ValueError("need at least n_taps frames of 8192 samples")
+    if coeffs is None:
+        key = (n_taps, adc.device.index)
+        coeffs = _pfb_coeff_cache.get(key)
+        if coeffs is None:
+            coeffs = torch.from_numpy(corr_pfb_coeffs(PFB_FFT, n_taps)).to(adc.device)
+            _pfb_coeff_cache[key] = coeffs
+    if out is None:
+        out = torch.empty((N, T, PFB_FFT // 2, 2), dtype=torch.float32, device=adc.device)
+    stride = adc.stride(0) if N > 1 else S  # a single row may carry any stride (e.g. a broadcast view)
+    corr_pfb(adc.data_ptr(), N, stride, S, n_taps, coeffs.data_ptr(), T, out.data_ptr(), _stream_handle(stream))
     return out
 
 

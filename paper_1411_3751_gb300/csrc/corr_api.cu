@@ -12,6 +12,8 @@
 
 #include "corr_internal.cuh"
 
+#include <cmath>
+
 using namespace corr;
 
 namespace {
@@ -746,6 +748,42 @@ int corr_requantize(const void* d_in, int in_type, int n_inputs, int n_time, int
                                        n_chans, gain, d_gains, symmetric != 0, static_cast<uint8_t*>(d_out),
                                        (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "corr_requantize: launch");
+  return CORR_OK;
+}
+
+int corr_pfb_coeffs(int n_fft, int n_taps, int32_t* h_out) {
+  if (!h_out) return fail(CORR_ERR_ARG, "corr_pfb_coeffs: NULL output");
+  if (n_fft < 2 || (n_fft & (n_fft - 1)) != 0 || n_taps < 1 || n_taps > 64 || (long long)n_fft * n_taps > (1 << 24))
+    return fail(CORR_ERR_ARG, "corr_pfb_coeffs: need n_fft a power of two >= 2 and 1 <= n_taps <= 64");
+  const long long L = (long long)n_fft * n_taps;
+  std::vector<double> h((size_t)L);
+  double peak = 0.0;
+  for (long long j = 0; j < L; ++j) {
+    const double w = L > 1 ? 0.54 - 0.46 * std::cos(2.0 * M_PI * (double)j / (double)(L - 1)) : 1.0;  // Hamming
+    const double u = ((double)j - 0.5 * (double)(L - 1)) / (double)n_fft;
+    const double sinc = u == 0.0 ? 1.0 : std::sin(M_PI * u) / (M_PI * u);
+    h[(size_t)j] = w * sinc;
+    peak = std::fabs(h[(size_t)j]) > peak ? std::fabs(h[(size_t)j]) : peak;
+  }
+  const double scale = 131071.0 / peak;  // 18-bit signed coefficients, largest magnitude 2^17 - 1
+  for (long long j = 0; j < L; ++j) h_out[j] = (int32_t)std::floor(h[(size_t)j] * scale + 0.5);
+  return CORR_OK;
+}
+
+int corr_pfb(const int8_t* d_adc, int n_inputs, long long input_stride, long long n_samples, int n_taps,
+             const int32_t* d_coeffs, int n_spectra, void* d_out, void* stream) {
+  constexpr long long M = 8192;
+  if (!d_adc || !d_coeffs || !d_out) return fail(CORR_ERR_ARG, "corr_pfb: NULL buffer");
+  if (n_inputs < 1 || n_inputs > 65535 || n_taps < 1 || n_taps > 64 || n_spectra < 0 || n_spectra > (1 << 30))
+    return fail(CORR_ERR_ARG, "corr_pfb: need 1 <= n_inputs <= 65535, 1 <= n_taps <= 64, n_spectra >= 0");
+  if (((long long)n_spectra + n_taps - 1) * M > n_samples || n_samples > input_stride)
+    return fail(CORR_ERR_ARG, "corr_pfb: need (n_spectra + n_taps - 1) * 8192 <= n_samples <= input_stride");
+  if ((input_stride & 3) != 0 || (reinterpret_cast<uintptr_t>(d_adc) & 3) != 0 ||
+      (reinterpret_cast<uintptr_t>(d_coeffs) & 15) != 0 || (reinterpret_cast<uintptr_t>(d_out) & 7) != 0)
+    return fail(CORR_ERR_ARG, "corr_pfb: samples and stride 4-byte, coefficients 16-byte, output 8-byte aligned");
+  const cudaError_t e = launch_pfb(d_adc, input_stride, n_inputs, n_spectra, n_taps, d_coeffs,
+                                   static_cast<float2*>(d_out), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_pfb: launch");
   return CORR_OK;
 }
 

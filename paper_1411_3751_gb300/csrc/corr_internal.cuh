@@ -134,6 +134,9 @@ cudaError_t launch_set_base(long long* d_base, const int* d_st, int n_st, long l
 // F-engine tail: gain, round, clip to 4+4 bits, channel selection and corner turn (requant.cu).
 cudaError_t launch_requant(const void* d_in, int in_type, int N, int T, int F, int chan0, int C, float gain,
                            const float* d_gains, int symmetric, uint8_t* d_out, cudaStream_t st);
+// PFB F-engine: int8 ADC frames -> FIR (exact int32) -> 8192-point real FFT -> float2 [N][T][4096] (pfb.cu).
+cudaError_t launch_pfb(const int8_t* d_adc, long long stride, int N, int T, int P, const int* d_h, float2* d_out,
+                       cudaStream_t st);
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
                         long long k_base, const Shape2& g, cudaStream_t st);
 

@@ -11,10 +11,13 @@
 * requant: the F-engine tail at the paper's sizes: 512 inputs x 1024 spectra of a 4096-channel PFB
   (18+18-bit integers), 2398 channels selected, requantised to 4+4 bits and corner-turned; bytes moved
   per second against the measured HBM copy bandwidth;
+* pfb: the PFB F-engine at the paper's sizes: 512 inputs, 4 taps, 8192-point real FFT, 64 spectra
+  (int8 ADC samples -> float32 channels); spectra per second against the 24 000 per second per input
+  a 196.608 MHz ADC produces;
 * fastdump: the 512-input x 2400-channel stream at the paper's minimum dump time (0.33 s = 8000
   samples, float32 visibilities) with 1 s total power of ten outrigger stations (selective dumps).
 
-    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream|fastdump|requant]
+    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream|fastdump|requant|pfb]
 """
 from __future__ import annotations
 
@@ -149,6 +152,31 @@ def requant(corr, synth, torch, reps=5):
             "real_time_factor": (T / 24000.0) / (ms / 1e3)}
 
 
+def pfb(corr, synth, torch, reps=5):
+    N, T, P = 512, 64, 4
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0x14113751 + 8)
+    adc = (torch.randn((N, (T + P - 1) * 8192), device="cuda", generator=g) * 20.0).round_().clamp_(-128, 127)
+    adc = adc.to(torch.int8)
+    out = torch.empty((N, T, 4096, 2), dtype=torch.float32, device="cuda")
+    corr.pfb(adc, P, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        corr.pfb(adc, P, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    spectra = N * T
+    # nominal flops of one spectrum: FIR 2 P M, complex FFT 5 (M/2) log2(M/2), split step ~ 10 (M/2)
+    flops = spectra * (2 * P * 8192 + 5 * 4096 * 12 + 10 * 4096)
+    moved = spectra * (8192 + 4096 * 8)  # one new ADC frame in, 4096 float32 complex channels out
+    return {"config": "pfb: N=512 inputs, 4 taps, 8192-point real FFT, 64 spectra", "ms": ms,
+            "spectra_per_s": spectra / (ms / 1e3), "tflops_nominal": flops / (ms / 1e3) / 1e12,
+            "gbs": moved / (ms / 1e3) / 1e9, "real_time_factor": (T / 24000.0) / (ms / 1e3)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="")
@@ -164,7 +192,7 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
-    todo = [a.only] if a.only else ["precision", "group", "stream", "fastdump", "requant"]
+    todo = [a.only] if a.only else ["precision", "group", "stream", "fastdump", "requant", "pfb"]
     for name in todo:
         if name == "precision":
             r = precision(corr, synth, torch)
@@ -174,6 +202,8 @@ def main(argv=None):
             r = fast_dump(corr, synth, torch)
         elif name == "requant":
             r = requant(corr, synth, torch)
+        elif name == "pfb":
+            r = pfb(corr, synth, torch)
         else:
             r = stream_loop(corr, synth, torch, a.stream_blocks)
         print(json.dumps({"measure": name, **r}))

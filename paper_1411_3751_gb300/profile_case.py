@@ -2,6 +2,7 @@
 
     python -m paper_1411_3751_gb300.profile_case --n 512 --c 128 --t 8192 --blocks 3 --path fp8tc
     python -m paper_1411_3751_gb300.profile_case --requant --n 512 --c 2398 --t 256 --blocks 3
+    python -m paper_1411_3751_gb300.profile_case --pfb --n 512 --t 16 --blocks 3
 
 Holds a single input block on the device (the same block is accumulated --blocks times), so the
 device footprint stays at a few GB for the 512-input, 128-channel case.
@@ -22,6 +23,8 @@ def main(argv=None):
     ap.add_argument("--blocks", type=int, default=3)
     ap.add_argument("--path", default="fp8tc")
     ap.add_argument("--seed", type=int, default=0x14113751 + 2)
+    ap.add_argument("--pfb", action="store_true",
+                    help="profile the PFB instead: --n inputs x --t spectra, 4 taps")
     ap.add_argument("--requant", action="store_true",
                     help="profile the requantiser instead: --n inputs x --t spectra of a 4096-channel PFB, "
                          "--c channels selected (int32 input)")
@@ -36,6 +39,17 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
+    if a.pfb:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(a.seed)
+        adc = (torch.randn((a.n, (a.t + 3) * 8192), device="cuda", generator=g) * 20.0).round_().clamp_(-128, 127)
+        adc = adc.to(torch.int8)
+        out = torch.empty((a.n, a.t, 4096, 2), dtype=torch.float32, device="cuda")
+        for _ in range(a.blocks):
+            corr.pfb(adc, 4, out=out)
+        torch.cuda.synchronize()
+        print("profile_case ok: pfb N=%d T=%d blocks=%d" % (a.n, a.t, a.blocks))
+        return
     if a.requant:
         g = torch.Generator(device="cuda")
         g.manual_seed(a.seed)

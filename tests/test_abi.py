@@ -76,3 +76,15 @@ def test_null_context_errors(lib):
     assert lib._lib.corr_dump(None, None, 1, 1, 0, 0, None) == lib.CORR_ERR_ARG
     assert "NULL context" in lib.corr_last_error()
     assert lib._lib.corr_destroy(None) == lib.CORR_OK
+
+
+def test_pfb_coeffs_match_the_oracle(lib):
+    """The library's host-side PFB prototype filter equals the oracle's independent computation."""
+    import numpy as np
+
+    from oracle import oracle
+
+    for n_fft, n_taps in ((8192, 4), (64, 3), (2, 1)):
+        np.testing.assert_array_equal(lib.corr_pfb_coeffs(n_fft, n_taps), oracle.pfb_coeffs(n_fft, n_taps))
+    with pytest.raises(lib.CorrError):
+        lib.corr_pfb_coeffs(100, 4)

@@ -357,3 +357,55 @@ def test_requantize_corner_turn_and_per_channel_gains():
                 assert got[t, c, n] == (((q[0] & 0xF) << 4) | (q[1] & 0xF))
     np.testing.assert_array_equal(oracle.requantize(x, 3, 7, gains=np.full(7, 1.25, np.float32)),
                                   oracle.requantize(x, 3, 7, gain=1.25))
+
+
+def test_pfb_coeffs_shape_symmetry_and_peak():
+    h = oracle.pfb_coeffs(8192, 4)
+    assert h.shape == (32768,) and np.abs(h).max() == 131071
+    np.testing.assert_array_equal(h, h[::-1])                      # linear phase
+    assert h[16383] == h[16384] == 131071                          # peak at the centre
+    assert abs(h[0]) < 131071 * 0.08 / 1000 + 1                    # Hamming end value 0.08 x a tiny sinc
+    g = oracle.pfb_coeffs(16, 3)
+    np.testing.assert_array_equal(g, g[::-1])
+
+
+def test_pfb_fir_and_dft_brute_force():
+    """Tiny PFB (M = 8, 3 taps) against plain loops: FIR sums and the DFT definition."""
+    rng = np.random.default_rng(3)
+    M, P, T, N = 8, 3, 5, 2
+    adc = rng.integers(-128, 128, size=(N, (T + P - 1) * M)).astype(np.int8)
+    h = oracle.pfb_coeffs(M, P)
+    X = oracle.pfb(adc, M, P)
+    for n in range(N):
+        for t in range(T):
+            y = [sum(int(h[p * M + m]) * int(adc[n, (t + p) * M + m]) for p in range(P)) for m in range(M)]
+            for k in range(M // 2):
+                want = sum(y[m] * np.exp(-2j * np.pi * k * m / M) for m in range(M)) / M
+                assert abs(X[n, t, k] - want) < 1e-9 * (1 + abs(want))
+
+
+def test_pfb_channel_response_of_a_tone():
+    """A tone at the centre of channel k0 lands in k0; the leakage follows the prototype filter's
+    response: -50 dB one channel away (the transition band of the 4-tap Hamming design), below -68 dB
+    two or more channels away, and a tone on a channel edge splits equally (-6 dB each)."""
+    M, P = 8192, 4
+    n = np.arange((P + 3) * M, dtype=np.float64)
+    for k0 in (100, 1500, 3000):
+        X = oracle.pfb(np.cos(2 * np.pi * k0 * n / M)[None, :], M, P)[0]
+        pw = np.abs(X).mean(axis=0) ** 2
+        assert np.argmax(pw) == k0
+        rel = 10 * np.log10(pw / pw[k0])
+        assert -51.0 < rel[k0 - 1] < -49.0 and -51.0 < rel[k0 + 1] < -49.0
+        far = np.r_[rel[k0 - 40:k0 - 1], rel[k0 + 2:k0 + 41]]
+        assert far.max() < -68.0
+    X = oracle.pfb(np.cos(2 * np.pi * 700.5 * n / M)[None, :], M, P)[0]
+    pw = np.abs(X).mean(axis=0) ** 2
+    assert abs(10 * np.log10(pw[700] / pw[701])) < 0.01
+
+
+def test_pfb_linearity():
+    rng = np.random.default_rng(9)
+    a = rng.standard_normal((2, 5 * 64))
+    b = rng.standard_normal((2, 5 * 64))
+    np.testing.assert_allclose(oracle.pfb(3 * a - 2 * b, 64, 4), 3 * oracle.pfb(a, 64, 4) - 2 * oracle.pfb(b, 64, 4),
+                               atol=1e-12)

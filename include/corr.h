@@ -292,6 +292,7 @@ int corr_xengine_static(const void* d_samples, int n_inputs, int n_chans, int n_
  *                     faster one (cached in-process by (N, C, T, n_pol, SM count), and in the file
  *                     named by CORR_AUTOTUNE_CACHE if set), then zeroes the accumulators it touched.
  *                     Synchronizes the stream. plans_out (optional) receives the chosen plans.
+ *                     A graph captured earlier is dropped (capture again afterwards).
  * corr_group_capture  records one grouped accumulate of the given buffers into a CUDA graph
  *                     (pointers are baked in: refill the same buffers before each replay); needs a
  *                     non-default stream.

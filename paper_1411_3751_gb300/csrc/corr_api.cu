@@ -1057,6 +1057,11 @@ int corr_group_autotune(corr_group* g, const void* const* d_samples, int* plans_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != CORR_OK) return rc;
+  // a captured graph refers to the old work list: drop it (corr_group_capture records a new one)
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
   return group_build_items(g);
 }
 

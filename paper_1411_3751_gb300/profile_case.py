@@ -23,6 +23,9 @@ def main(argv=None):
     ap.add_argument("--blocks", type=int, default=3)
     ap.add_argument("--path", default="fp8tc")
     ap.add_argument("--seed", type=int, default=0x14113751 + 2)
+    ap.add_argument("--batch", action="store_true",
+                    help="accumulate the block --blocks times in one corr_accumulate_batch call (the X-engine "
+                         "launches then build the next block's operand in their background warps)")
     ap.add_argument("--pfb", action="store_true",
                     help="profile the PFB instead: --n inputs x --t spectra, 4 taps")
     ap.add_argument("--requant", action="store_true",
@@ -62,8 +65,11 @@ def main(argv=None):
         return
     x = synth.generate_device(synth.Spec(kind="gauss_tone", seed=a.seed), a.t, a.c, a.n)
     with corr.Correlator(a.n, a.c, a.t, a.npol, path=a.path) as xc:
-        for _ in range(a.blocks):
-            xc.accumulate(x)
+        if a.batch:
+            xc.accumulate_batch([x] * a.blocks)
+        else:
+            for _ in range(a.blocks):
+                xc.accumulate(x)
         xc.dump(corr.CORR_WHAT_CROSS)
         xc.sync()
     torch.cuda.synchronize()

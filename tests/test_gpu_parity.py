@@ -132,6 +132,24 @@ def test_batch_equals_sequential(env, path):
     assert np.array_equal(c.cpu().numpy(), want_c) and np.array_equal(a.cpu().numpy(), want_a)
 
 
+@pytest.mark.parametrize("shape", [(200, 3, 4096, 7, 2), (96, 2, 2048, 9, 1), (512, 2, 8192, 3, 2), (6, 1, 8192, 3, 2)])
+def test_batch_over_several_launches(env, shape):
+    """Batches longer than one tensor-core launch (chunks of about 8192 samples, several blocks per
+    chunk for short blocks); N not a multiple of 16 takes the byte-load path of the operand build."""
+    corr, synth, torch = env
+    N, C, T, B, npol = shape
+    blocks = [synth.generate_device(synth.Spec(kind="saturate", seed=700 + b, seg_len=512, m8_segment=1), T, C, N)
+              for b in range(B)]
+    host = np.concatenate([b.cpu().numpy() for b in blocks])
+    want_c, want_a = oracle.correlate(host, npol, threads=8)
+    with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+        xc.accumulate_batch(blocks)
+        c = xc.dump(corr.CORR_WHAT_CROSS)
+        a = xc.dump(corr.CORR_WHAT_AUTO)
+        xc.sync()
+    assert np.array_equal(c.cpu().numpy(), want_c) and np.array_equal(a.cpu().numpy(), want_a)
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_dump_formats_host_and_reset(env, path):
     corr, synth, torch = env

@@ -330,11 +330,24 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        # the host link on this machine: plain pinned copies of the same blocks, same process
+        scratch = torch.empty_like(blocks[0])
+        scratch.copy_(host_blocks[0], non_blocking=True)
+        torch.cuda.synchronize()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record()
+        for b in range(N_BLOCKS):
+            scratch.copy_(host_blocks[b], non_blocking=True)
+        l1.record()
+        torch.cuda.synchronize()
+        h2d = N_BLOCKS * T_BLOCK * N_CHAN * N_IN
+        link_gbs = h2d / (l0.elapsed_time(l1) / 1e3) / 1e9
         e2e = {"value": cm_step * args.e2e_steps * world / (e_ms / 1e3) / 1e12, "unit": "Tera-CMAC/s",
-               "h2d_bytes_per_step": N_BLOCKS * T_BLOCK * N_CHAN * N_IN,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": cross_h.numel() * 8 + autos_h.numel() * 8,
-               "ms_per_step": e_ms / args.e2e_steps}
-        del host_blocks
+               "ms_per_step": e_ms / args.e2e_steps,
+               "link_h2d_gbs": link_gbs, "link_bound_ms_per_step": h2d / link_gbs / 1e6}
+        del host_blocks, scratch
 
     # same-GPU comparison legs of the metric on the same workload: the integer tensor path
     # (mma.sync s8) and the FP32 CUDA-core path (the paper's arithmetic)

@@ -389,7 +389,7 @@ def main():
             "real_time_factor": rtf,
             "roofline": roof,
             "kernel_ms_per_step": {"xeng": xeng_ms / args.steps, "unpack": unpack_ms / args.steps,
-                                   "autos_side_stream": autos_ms / args.steps, "dump": dump_ms / args.steps},
+                                   "autos": autos_ms / args.steps, "dump": dump_ms / args.steps},
             "gpu_launches": (xeng_n + unpack_n + dump_n + autos_n),
             "gpu_launches_per_step": launches_per_step,
             "clocks": clk,

@@ -71,6 +71,15 @@ def test_ragged_shapes(env, path, shape):
     _check(env, host, npol, path)
 
 
+@pytest.mark.parametrize("path", ["fp32", "i8mma", "fp8tc"])
+def test_large_array_2048_inputs(env, path):
+    """N = 2048 (1024 dual-pol stations, four times the paper's array): many tiles per channel and
+    more than 2^20 station-pair cells per channel; full oracle comparison."""
+    _, synth, _ = env
+    host = synth.generate_host(synth.Spec(kind="gauss_tone", seed=2048), 384, 2, 2048)
+    _check(env, host, 2, path)
+
+
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("byte,expect_re", [(0x88, 128), (0x77, 98)])
 def test_extremes_closed_form(env, path, byte, expect_re):

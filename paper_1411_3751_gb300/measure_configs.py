@@ -1,5 +1,8 @@
 """Measurements of the secondary workloads (one JSON line each):
 
+* tiny: 32 inputs x 8 channels x 1024 samples (uniform components), each arithmetic path; a launch-
+  bound case (the FP32 path is the paper's arithmetic);
+
 * precision: 512 inputs x 256 channels x 65536 samples with saturation-heavy segments; X-engine time
   with in-chip partial sums flushed to int64 every 4096 / 16384 / 65536 samples on the FP8 tcgen05
   path and every 16384 / 65536 samples on the int8 mma.sync path (the flush overhead is the
@@ -17,7 +20,7 @@
 * fastdump: the 512-input x 2400-channel stream at the paper's minimum dump time (0.33 s = 8000
   samples, float32 visibilities) with 1 s total power of ten outrigger stations (selective dumps).
 
-    python -m paper_1411_3751_gb300.measure_configs [--only precision|group|stream|fastdump|requant|pfb]
+    python -m paper_1411_3751_gb300.measure_configs [--only tiny|precision|group|stream|fastdump|requant|pfb]
 """
 from __future__ import annotations
 
@@ -29,6 +32,27 @@ import sys
 
 def _useful(N, C, T):
     return N * (N + 1) // 2 * C * T
+
+
+def tiny(corr, synth, torch, reps=200):
+    N, C, T, npol = 32, 8, 1024, 2
+    x = synth.generate_device(synth.Spec(kind="uniform", seed=0x14113751 + 1), T, C, N)
+    out = {"config": "tiny: N=32, C=8, T=1024, uniform"}
+    for path in ("fp32", "i8mma", "fp8tc"):
+        with corr.Correlator(N, C, T, npol, path=path) as xc:
+            for _ in range(3):
+                xc.accumulate(x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                xc.accumulate(x)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        out[path] = {"ms_per_block": ms, "tcmac_s": _useful(N, C, T) / (ms / 1e3) / 1e12,
+                     "real_time_factor": (T / 24000.0) / (ms / 1e3)}
+    return out
 
 
 def precision(corr, synth, torch, reps=3):
@@ -192,9 +216,11 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
-    todo = [a.only] if a.only else ["precision", "group", "stream", "fastdump", "requant", "pfb"]
+    todo = [a.only] if a.only else ["tiny", "precision", "group", "stream", "fastdump", "requant", "pfb"]
     for name in todo:
-        if name == "precision":
+        if name == "tiny":
+            r = tiny(corr, synth, torch)
+        elif name == "precision":
             r = precision(corr, synth, torch)
         elif name == "group":
             r = group(corr, synth, torch)

@@ -94,7 +94,11 @@ typedef enum corr_kernel {
  */
 corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol);
 
-/* Select the arithmetic path (corr_path). Any time; accumulated sums are exact on every path. */
+/* Select the arithmetic path (corr_path). Any time; accumulated sums are exact on every path.
+ * corr_create allocates the operand scratch of the default tensor path; selecting CORR_PATH_FP32 or
+ * CORR_PATH_I8MMA waits for the device and releases it (the context then holds
+ * corr_footprint_bytes(..., path)); selecting a tensor path again allocates it (CORR_ERR_OOM if it
+ * no longer fits). */
 int corr_set_path(corr_ctx* ctx, int path);
 
 /* Return the path that corr_accumulate will run (AUTO resolved). */

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <new>
 #include <string>
 #include <tuple>
@@ -94,7 +95,8 @@ size_t in_stage_bytes(const Layout& L) {
 size_t footprint(const Layout& L, int path) {
   size_t b = (size_t)(L.cross_elems + L.autos_elems) * 8 + (size_t)L.autos_elems * 32 + 256;
   b += 2 * kStageBytes + 2 * in_stage_bytes(L);
-  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) b += L.op_buf_bytes;  // operand scratch
+  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO || path == CORR_PATH_FP8TC_FUSED)
+    b += L.op_buf_bytes;  // operand scratch (the fused path falls back to two passes for some shapes)
   const long long nb = (L.s.N + 63) / 64;
   b += (size_t)(nb * (nb + 1) / 2) * sizeof(int2) + (size_t)(nb * 8 + 8) * sizeof(F8Tile);
   return b;
@@ -112,6 +114,19 @@ std::vector<int2> fp32_tiles(int N) {
 
 namespace corr {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+cudaError_t set_smem_limit(const void* func, int bytes) {
+  static std::mutex m;
+  static std::set<std::pair<const void*, int>> done;  // (kernel, device)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(m);
+  if (done.count({func, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert({func, dev});
+  return e;
+}
 }  // namespace corr
 
 // Opt-in per-kernel timing: CUDA events recorded on the launching stream around each launch.
@@ -483,9 +498,15 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
 int corr_set_path(corr_ctx* c, int path) {
   if (!c) return fail(CORR_ERR_ARG, "corr_set_path: NULL context");
   if (!valid_path(path)) return fail(CORR_ERR_ARG, "corr_set_path: unknown path " + std::to_string(path));
-  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO) {
-    const int rc = ensure_operand_scratch(c);
+  if (path == CORR_PATH_FP8TC || path == CORR_PATH_AUTO || path == CORR_PATH_FP8TC_FUSED) {
+    const int rc = ensure_operand_scratch(c);  // the fused path falls back to two passes for some shapes
     if (rc != CORR_OK) return rc;
+  } else if (c->d_op) {
+    // FP32 and int8 paths unpack in shared memory: release the operand scratch once queued work is done
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "corr_set_path: synchronize");
+    cudaFree(c->d_op);
+    c->d_op = nullptr;
   }
   c->path = path;
   return CORR_OK;
@@ -915,6 +936,10 @@ int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
   const int T_pad = c0->L.T_pad;
   XengArgs a;
   std::memset(&a, 0, sizeof(a));
+  for (int i = 0; i < g->n; ++i)
+    if (!g->ctx[i]->d_op)
+      return fail(CORR_ERR_STATE, "group member " + std::to_string(i) +
+                                      " has no operand scratch (its path was set to FP32 or int8; set a tensor path)");
   for (int i = 0; i < g->n; ++i) {
     corr_ctx* c = g->ctx[i];
     bool tb = timer_begin(c0, CORR_KERNEL_UNPACK, st);

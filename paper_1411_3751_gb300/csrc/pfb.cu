@@ -218,12 +218,8 @@ cudaError_t launch_pfb(const int8_t* d_adc, long long stride, int N, int T, int 
   if (e == cudaSuccess) e = ensure_twiddles(dev);
   if (e != cudaSuccess) return e;
   constexpr int smem = PFB_SPB * PFB_ZLEN * (int)sizeof(float2);
-  static bool attr_set = false;  // per process: the attribute is a property of the function
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(pfb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  e = set_smem_limit(reinterpret_cast<const void*>(pfb_kernel), smem);
+  if (e != cudaSuccess) return e;
   pfb_kernel<<<dim3((unsigned)((T + PFB_SPB - 1) / PFB_SPB), (unsigned)N), PFB_NT, smem, st>>>(d_adc, stride, T, P,
                                                                                               d_h, d_out);
   return cudaGetLastError();

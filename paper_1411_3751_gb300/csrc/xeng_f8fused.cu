@@ -300,11 +300,9 @@ bool f8_fused_supported(const Shape& s, const void* d_in, int T_blk) {
 cudaError_t launch_f8_fused(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const F8Tile* d_tiles,
                             int n_tiles, long long* d_cross, long long* d_autos, int* d_err, int num_sms,
                             cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(f8_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  {
+    const cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_fused_kernel), SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const long long total = (long long)n_tiles * s.C;
   const int T_run = (int)round_up(T_blk, KT);

@@ -337,11 +337,9 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
 }
 
 cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(f8_xeng_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  {
+    const cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel), SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   if (args.n_items == 0 || args.T_run == 0) return cudaSuccess;
   const int grid = (int)(args.n_items < num_sms ? args.n_items : num_sms);

@@ -200,11 +200,9 @@ __global__ void __launch_bounds__(NT, 2)
 cudaError_t launch_i8mma(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const int2* d_tiles,
                          int n_tiles, long long* d_cross, long long* d_autos, cudaStream_t st) {
   if (n_tiles == 0 || T_blk == 0) return cudaSuccess;
-  static bool attr_set = false;  // per process: the attribute is a property of the function
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(xeng_i8mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  {
+    const cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(xeng_i8mma_kernel), SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const bool vec = (s.N & 3) == 0 && (reinterpret_cast<uintptr_t>(d_in) & 3) == 0;
   xeng_i8mma_kernel<<<dim3(n_tiles, s.C), NT, SMEM_BYTES, st>>>(d_in, s.N, s.C, T_blk, s.npol, s.Bs, flush_len,

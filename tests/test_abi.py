@@ -53,7 +53,7 @@ def test_host_only_helpers(lib):
     assert fp >= acc + 128 * 8192 * 1024  # operand scratch of the two-pass tensor path
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_AUTO) == fp
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP32) < fp
-    assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP8TC_FUSED) < fp
+    assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_FP8TC_FUSED) == fp  # may fall back to two passes
     assert lib.corr_footprint_bytes(512, 128, 8192, 2, lib.CORR_PATH_I8MMA) < fp  # no operand scratch
     assert lib.corr_footprint_bytes(4, 65536, 1, 2, lib.CORR_PATH_FP32) == 0     # channel limit
     assert lib.corr_footprint_bytes(0, 1, 1, 1, 0) == 0

@@ -140,3 +140,26 @@ def test_five_uneven_subarrays_graph(env):
                 assert np.array_equal(autos[f], oracle.autos(xf[:, None, :])[0]), (i, f)
                 assert _freivalds(xf, cross[f], npol, rng), (i, f)
     print("five-array group: tile plans %s" % plans)
+
+
+def test_member_path_switch_releases_scratch_and_group_rejects_it(env):
+    """Setting a member to the FP32 path releases its operand scratch; the grouped launch then refuses
+    with an error (no launch on a missing buffer) and works again once a tensor path is set."""
+    corr, synth, torch = env
+    shapes = [(64, 8), (512, 16)]
+    T, npol = 1024, 2
+    blocks = [synth.generate_device(synth.Spec(kind="gauss_tone", seed=90 + i), T, c, n) for i, (n, c) in enumerate(shapes)]
+    with corr.Group(shapes, T, npol) as g:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        g.members[1].set_path("fp32")
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 - free0 >= 100 << 20  # 16 ch x 1024 samples x 1024 rows x 8 blocks per launch
+        with pytest.raises(corr.CorrError):
+            g.accumulate(blocks)
+        g.members[1].set_path("fp8tc")
+        g.accumulate(blocks)
+        for i, m in enumerate(g.members):
+            c, a = _dump(m, corr)
+            want_c, want_a = oracle.correlate(blocks[i].cpu().numpy(), npol, threads=8)
+            assert np.array_equal(c, want_c) and np.array_equal(a, want_a), i

@@ -1,82 +1,107 @@
 // FP32 CUDA-core X-engine: the same arithmetic class as the paper's GPU layer (FP32 FMA on CUDA
 // cores over 8+8-bit promoted samples, Sec. 2.4-2.5), used as the same-GPU comparison path.
 //
-// One CTA computes a 64 x 64 block of inputs (i = a-side row block, j = c-side column block,
-// block(i) >= block(j), so only the lower block triangle is visited) for one channel. Each of the
-// 128 threads holds an 8 (i) x 4 (j) register tile of complex FP32 partial sums. Samples are
-// staged per 32-sample slice in shared memory as float2 (sign-extended nibbles). Every
-// `flush_len` samples (<= 65536) the partials, which are exact integers of magnitude
-// <= 128 * 65536 = 2^23, are converted to int64 and added to the accumulators.
+// One CTA of 64 threads computes a 64 x 64 block of inputs (i = a-side row block, j = c-side column
+// block, block(i) >= block(j), so only the lower block triangle is visited) for one channel. Each
+// thread holds an 8 (i) x 8 (j) register tile of complex FP32 partial sums: per sample it reads 8 + 8
+// complex values from shared memory and issues 256 FMAs. Samples are staged 32 at a time in shared
+// memory as float2 (sign-extended nibbles); the raw bytes of the next 32 samples are loaded into
+// registers while the current ones are multiplied. Every `flush_len` samples (<= 65536) the partials,
+// exact integers of magnitude <= 128 * 65536 = 2^23, are converted to int64 and added to the
+// accumulators.
 #include "corr_internal.cuh"
 
 namespace corr {
 namespace {
 
-constexpr int TI = 64, TJ = 64, KT = kF32Kt, NT = 128;
-constexpr int UI = 8, UJ = 4;  // per-thread tile
+constexpr int TB = 64, KT = kF32Kt, NT = 64;
+constexpr int U = 8;  // per-thread tile: U x U complex
+constexpr int WORDS = KT * 2 * (TB / 4) / NT;  // raw 4-byte words per thread per stage (16)
 
 __device__ __forceinline__ float nib(unsigned v) { return (float)(((int)(v & 0xF) ^ 8) - 8); }
 
+// Raw bytes of inputs x0 + 4 w .. + 3 at time t (zero outside the block or the input range).
+__device__ __forceinline__ uint32_t raw_word(const uint8_t* __restrict__ in, int N, int C, int f, int T, int t, int x0,
+                                             int w, bool vec) {
+  const int n = x0 + 4 * w;
+  if (t >= T || n >= N) return 0u;
+  const uint8_t* p = in + ((size_t)t * C + f) * N + n;
+  if (vec) return __ldg(reinterpret_cast<const unsigned*>(p));  // N % 4 == 0, aligned base
+  uint32_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (n + k < N) v |= (uint32_t)__ldg(p + k) << (8 * k);
+  return v;
+}
+
 __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int npol,
                                                        long long Bs, int flush_len, const int2* __restrict__ tiles,
-                                                       long long* __restrict__ cross, long long* __restrict__ autos) {
-  __shared__ __align__(16) float2 xi_s[KT][TI];
-  __shared__ __align__(16) float2 xj_s[KT][TJ];
+                                                       bool vec, long long* __restrict__ cross,
+                                                       long long* __restrict__ autos) {
+  __shared__ __align__(16) float2 xi_s[KT][TB];
+  __shared__ __align__(16) float2 xj_s[KT][TB];
   const int2 tb = tiles[blockIdx.x];
   const int f = blockIdx.y;
-  const int i0 = tb.x * TI, j0 = tb.y * TJ;
+  const int i0 = tb.x * TB, j0 = tb.y * TB;
   const int tid = threadIdx.x;
-  const int ig = tid >> 4, jg = tid & 15;
+  const int ig = tid >> 3, jg = tid & 7;
   const int P = npol * npol;
 
-  float are[UI][UJ], aim[UI][UJ];
+  // staging: word q of this thread (q < WORDS) = side q / 8, sample (tid + 64 (q % 8)) / 16 ... laid
+  // out so that 16 consecutive threads read the 16 words (64 inputs) of one sample row
+  uint32_t raw[WORDS];
+  auto load = [&](int t0) {
 #pragma unroll
-  for (int u = 0; u < UI; ++u)
+    for (int q = 0; q < WORDS; ++q) {
+      const int e = tid + NT * (q & 7);  // 0 .. 511 per side
+      const int tt = e >> 4, w = e & 15;
+      raw[q] = raw_word(in, N, C, f, T, t0 + tt, q < 8 ? i0 : j0, w, vec);
+    }
+  };
+  auto store = [&]() {
 #pragma unroll
-    for (int v = 0; v < UJ; ++v) are[u][v] = aim[u][v] = 0.f;
+    for (int q = 0; q < WORDS; ++q) {
+      const int e = tid + NT * (q & 7);
+      const int tt = e >> 4, w = e & 15;
+      float2* dst = (q < 8 ? &xi_s[tt][4 * w] : &xj_s[tt][4 * w]);
+      const uint32_t v = raw[q];
+      const float4 lo = make_float4(nib(v >> 4), nib(v), nib(v >> 12), nib(v >> 8));
+      const float4 hi = make_float4(nib(v >> 20), nib(v >> 16), nib(v >> 28), nib(v >> 24));
+      reinterpret_cast<float4*>(dst)[0] = lo;
+      reinterpret_cast<float4*>(dst)[1] = hi;
+    }
+  };
+
+  float are[U][U], aim[U][U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) are[u][v] = aim[u][v] = 0.f;
 
   int since_flush = 0;
+  load(0);
   for (int t0 = 0; t0 < T; t0 += KT) {
+    __syncthreads();  // previous stage fully consumed
+    store();
     __syncthreads();
-    for (int e = tid; e < KT * TI; e += NT) {
-      const int tt = e / TI, n = e % TI;
-      float2 vi = make_float2(0.f, 0.f), vj = make_float2(0.f, 0.f);
-      if (t0 + tt < T) {
-        const uint8_t* row = in + ((size_t)(t0 + tt) * C + f) * N;
-        if (i0 + n < N) {
-          const unsigned b = row[i0 + n];
-          vi = make_float2(nib(b >> 4), nib(b));
-        }
-        if (j0 + n < N) {
-          const unsigned b = row[j0 + n];
-          vj = make_float2(nib(b >> 4), nib(b));
-        }
-      }
-      xi_s[tt][n] = vi;
-      xj_s[tt][n] = vj;
-    }
-    __syncthreads();
-#pragma unroll 4
+    if (t0 + KT < T) load(t0 + KT);  // next stage's bytes in flight during the multiply
+#pragma unroll 2
     for (int tt = 0; tt < KT; ++tt) {
-      float2 a[UI], b[UJ];
-      const float4* pa = reinterpret_cast<const float4*>(&xi_s[tt][ig * UI]);
-      const float4* pb = reinterpret_cast<const float4*>(&xj_s[tt][jg * UJ]);
+      float2 a[U], b[U];
+      const float4* pa = reinterpret_cast<const float4*>(&xi_s[tt][ig * U]);
+      const float4* pb = reinterpret_cast<const float4*>(&xj_s[tt][jg * U]);
 #pragma unroll
-      for (int u = 0; u < UI / 2; ++u) {
-        const float4 q = pa[u];
-        a[2 * u] = make_float2(q.x, q.y);
-        a[2 * u + 1] = make_float2(q.z, q.w);
+      for (int h = 0; h < U / 2; ++h) {
+        const float4 qa = pa[h], qb = pb[h];
+        a[2 * h] = make_float2(qa.x, qa.y);
+        a[2 * h + 1] = make_float2(qa.z, qa.w);
+        b[2 * h] = make_float2(qb.x, qb.y);
+        b[2 * h + 1] = make_float2(qb.z, qb.w);
       }
 #pragma unroll
-      for (int v = 0; v < UJ / 2; ++v) {
-        const float4 q = pb[v];
-        b[2 * v] = make_float2(q.x, q.y);
-        b[2 * v + 1] = make_float2(q.z, q.w);
-      }
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int u = 0; u < UI; ++u)
-#pragma unroll
-        for (int v = 0; v < UJ; ++v) {
+        for (int v = 0; v < U; ++v) {
           // x_i conj(x_j) = (ar + i ai)(br - i bi)
           are[u][v] = fmaf(a[u].x, b[v].x, are[u][v]);
           are[u][v] = fmaf(a[u].y, b[v].y, are[u][v]);
@@ -88,11 +113,11 @@ __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict
     if (since_flush >= flush_len || t0 + KT >= T) {
       since_flush = 0;
 #pragma unroll
-      for (int u = 0; u < UI; ++u) {
-        const int i = i0 + ig * UI + u;
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + ig * U + u;
 #pragma unroll
-        for (int v = 0; v < UJ; ++v) {
-          const int j = j0 + jg * UJ + v;
+        for (int v = 0; v < U; ++v) {
+          const int j = j0 + jg * U + v;
           const long long re = __float2ll_rn(are[u][v]);
           const long long im = __float2ll_rn(aim[u][v]);
           are[u][v] = aim[u][v] = 0.f;
@@ -115,8 +140,10 @@ __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict
 cudaError_t launch_fp32(const Shape& s, const uint8_t* d_in, int T_blk, int flush_len, const int2* d_tiles,
                         int n_tiles, long long* d_cross, long long* d_autos, cudaStream_t st) {
   if (n_tiles == 0 || T_blk == 0) return cudaSuccess;
+  const bool vec = (s.N & 3) == 0 && (reinterpret_cast<uintptr_t>(d_in) & 3) == 0;
   dim3 grid(n_tiles, s.C);
-  xeng_fp32_kernel<<<grid, NT, 0, st>>>(d_in, s.N, s.C, T_blk, s.npol, s.Bs, flush_len, d_tiles, d_cross, d_autos);
+  xeng_fp32_kernel<<<grid, NT, 0, st>>>(d_in, s.N, s.C, T_blk, s.npol, s.Bs, flush_len, d_tiles, vec, d_cross,
+                                        d_autos);
   return cudaGetLastError();
 }
 

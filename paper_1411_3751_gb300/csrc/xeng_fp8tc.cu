@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   uint32_t sre[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
   uint32_t sim[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
   if (g < G) {
-    // 4 samples per thread per iteration, all loads issued before any conversion
-    constexpr int U = 4;
+    // 8 samples per thread per iteration, all loads issued before any conversion
+    constexpr int U = 8;
     for (int t0 = t_begin + 4 * warp + tl; t0 < t_end; t0 += 32 * U) {
       uint4 w[U];
       bool live[U];

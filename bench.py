@@ -41,8 +41,9 @@ def useful_cmacs(N, C, T):
     return N * (N + 1) // 2 * C * T
 
 
-def profiled_traffic(kernel_files, profile_md):
-    """DRAM bytes per launch recorded by an ncu capture (profiles/), if the kernel sources still match."""
+def profiled_traffic(kernel_files, profile_md, blocks_per_launch):
+    """DRAM bytes per launch recorded by an ncu capture (profiles/), if the kernel sources still match
+    and the capture covered launches of the same size."""
     import hashlib
 
     try:
@@ -50,8 +51,11 @@ def profiled_traffic(kernel_files, profile_md):
         h = hashlib.sha256()
         for f in kernel_files:
             h.update(open(os.path.join(ROOT, "paper_1411_3751_gb300", "csrc", f), "rb").read())
-        vals = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+        keys = ("traffic_bytes_per_launch:", "source_sha256:", "blocks_per_launch:")
+        vals = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(keys))
         if vals.get("source_sha256", "").strip() != h.hexdigest()[:16]:
+            return None
+        if abs(float(vals.get("blocks_per_launch", "1")) - blocks_per_launch) > 1e-9:
             return None
         return int(vals["traffic_bytes_per_launch"])
     except Exception:
@@ -298,8 +302,9 @@ def main():
         bound = "alu"
     achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
     traffic = None
-    if args.path == "fp8tc" and abs(blocks_per_launch - 1.0) < 1e-9:
-        traffic = profiled_traffic(["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"], "f8_xeng_512in_128ch_8192.md")
+    if args.path == "fp8tc":
+        traffic = profiled_traffic(["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"], "f8_xeng_512in_128ch_8192.md",
+                                   blocks_per_launch)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel",
                                            "i8mma": "xeng_i8mma_kernel"}.get(args.path, "xeng_fp32_kernel"),

@@ -74,10 +74,14 @@ Layout make_layout(int N, int C, int T, int npol) {
   if (!mul_ok((unsigned long long)C * (unsigned long long)L.T_pad, (unsigned long long)L.R, &ob) || ob > (1ull << 46))
     return L;
   L.op_bytes = ob;
-  // blocks per batch launch: about kBatchSamples samples per launch (longer launches lose the L2
-  // reuse of a channel's operand between its tiles), never beyond the exactness bound of an
-  // in-chip partial sum (kF8MaxFlush), and a buffer is capped at kMaxOperandBuffer
-  long long k = kBatchSamples / L.T_pad;
+  // blocks per batch launch: the operand of the channels in flight within kL2Window (see there),
+  // at most kF8MaxFlush samples per launch, and a buffer is capped at kMaxOperandBuffer
+  const long long tiles_per_chan = (long long)f8_tile_plan(N, L.R, 0).size();
+  double in_flight = (double)kSmCount / (double)(tiles_per_chan > 0 ? tiles_per_chan : 1);
+  if (in_flight < 1.0) in_flight = 1.0;
+  const double t_launch = (double)kL2Window / (in_flight * (double)L.R);
+  long long k = (long long)(t_launch / (double)L.T_pad);
+  if (k * L.T_pad > kF8MaxFlush) k = kF8MaxFlush / L.T_pad;
   if (k < 1) k = 1;
   const long long kmem = ob > 0 ? (long long)(kMaxOperandBuffer / ob) : 1;
   if (k > kmem) k = kmem < 1 ? 1 : kmem;

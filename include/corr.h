@@ -124,9 +124,9 @@ int corr_accumulate(corr_ctx* ctx, const void* d_samples, void* cuda_stream);
 /*
  * corr_accumulate_batch - add n_blocks blocks, d_blocks[b] each a device uint8[T][C][N], in order;
  * the result equals n_blocks corr_accumulate calls (the paper integrates 27 groups of spectra per
- * dump, Sec. 2.5). Short blocks share tensor-core launches (about 8192 samples per launch), so the
- * int64 flush and the launch cost are paid once per group of blocks. The pointer array is read
- * during the call only.
+ * dump, Sec. 2.5). Consecutive blocks share tensor-core launches (as many as keep the operand of the
+ * channels in flight within L2: 4 blocks of 8192 samples at 512 inputs), so the int64 flush and the
+ * launch cost are paid once per group of blocks. The pointer array is read during the call only.
  */
 int corr_accumulate_batch(corr_ctx* ctx, const void* const* d_blocks, int n_blocks, void* cuda_stream);
 

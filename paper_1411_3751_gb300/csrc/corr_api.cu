@@ -369,11 +369,12 @@ int ensure_operand_scratch(corr_ctx* c) {
   return CORR_OK;
 }
 
-// n blocks through the two-pass tensor path in chunks of up to K_batch blocks (about 8192 samples
-// per launch): the operand of a chunk is built with each block at its own sample offset, then one
-// tensor-core launch multiplies the whole chunk, so short blocks share launches and flushes. (Building
-// the next chunk on a second stream while this one multiplies was measured: both kernels then share
-// HBM bandwidth and the step time does not change, so the chunks run in order on the caller's stream.)
+// n blocks through the two-pass tensor path in chunks of up to K_batch blocks (launch length from the
+// L2 budget, see kL2Window): the operand of a chunk is built with each block at its own sample
+// offset, then one tensor-core launch multiplies the whole chunk, so blocks share launches and
+// flushes. (Building the next chunk while this one multiplies gains nothing: on a second stream the
+// persistent X-engine holds every SM, and inside it the extra load/store traffic slows its epilogue;
+// the chunks run in order on the caller's stream.)
 int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
   const int T_blk = c->L.s.T;
   const int T_pad = c->L.T_pad;

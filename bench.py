@@ -216,7 +216,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp8tc_fused", "i8mma", "fp32"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--i8-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -329,12 +329,18 @@ def main():
         torch.cuda.synchronize()
         barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        marks = []
         e0.record(stream)
         for _ in range(args.e2e_steps):
             e2e_step()
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        # per-step times, so that a sporadic stall of the host link shows as such
+        per_step = sorted([e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k])
+                                                          for k in range(1, len(marks))])
         # the host link on this machine: plain pinned copies of the same blocks, same process
         scratch = torch.empty_like(blocks[0])
         scratch.copy_(host_blocks[0], non_blocking=True)
@@ -351,6 +357,7 @@ def main():
                "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": cross_h.numel() * 8 + autos_h.numel() * 8,
                "ms_per_step": e_ms / args.e2e_steps,
+               "ms_per_step_median": per_step[len(per_step) // 2], "ms_per_step_max": per_step[-1],
                "link_h2d_gbs": link_gbs, "link_bound_ms_per_step": h2d / link_gbs / 1e6}
         del host_blocks, scratch
 

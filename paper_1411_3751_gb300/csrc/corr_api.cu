@@ -37,7 +37,9 @@ struct Layout {
   Shape s;
   long long cross_elems;  // int64 elements
   long long autos_elems;
-  int R;                  // FP8 operand rows
+  int R;                  // FP8 operand rows per sample as the tiles see them: round_up(2N, 128)
+  int R_buf;              // operand rows stored per sample: round_up(2N, 32); the TMA fills rows
+                          // R_buf .. R - 1 of a tile with zeros (out of the tensor map's extent)
   int T_pad;              // FP8 operand samples per channel and block
   size_t op_bytes;        // one block's operand
   int K_batch;            // blocks per operand buffer (one tensor-core launch in a batch)
@@ -69,9 +71,10 @@ Layout make_layout(int N, int C, int T, int npol) {
   L.cross_elems = (long long)x;
   L.autos_elems = (long long)C * N;
   L.R = (int)round_up(2LL * N, kF8RowAlign);
+  L.R_buf = (int)round_up(2LL * N, 32);
   L.T_pad = (int)round_up(T, kF8Kt);
   unsigned long long ob;
-  if (!mul_ok((unsigned long long)C * (unsigned long long)L.T_pad, (unsigned long long)L.R, &ob) || ob > (1ull << 46))
+  if (!mul_ok((unsigned long long)C * (unsigned long long)L.T_pad, (unsigned long long)L.R_buf, &ob) || ob > (1ull << 46))
     return L;
   L.op_bytes = ob;
   // blocks per batch launch: the operand of the channels in flight within kL2Window (see there),
@@ -79,7 +82,7 @@ Layout make_layout(int N, int C, int T, int npol) {
   const long long tiles_per_chan = (long long)f8_tile_plan(N, L.R, 0).size();
   double in_flight = (double)kSmCount / (double)(tiles_per_chan > 0 ? tiles_per_chan : 1);
   if (in_flight < 1.0) in_flight = 1.0;
-  const double t_launch = (double)kL2Window / (in_flight * (double)L.R);
+  const double t_launch = (double)kL2Window / (in_flight * (double)L.R_buf);
   long long k = (long long)(t_launch / (double)L.T_pad);
   if (k * L.T_pad > kF8MaxFlush) k = kF8MaxFlush / L.T_pad;
   if (k < 1) k = 1;
@@ -281,7 +284,7 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
     const int T_run = (int)round_up(T_blk, kF8Kt);
     const bool two_pass = path == CORR_PATH_FP8TC || !f8_fused_supported(c->L.s, d_in, T_blk);
     bool tb = timer_begin(c, CORR_KERNEL_UNPACK, st);
-    e = launch_f8_prep(c->L.s, d_in, T_blk, T_run, c->L.T_pad * c->L.K_batch, 0, c->L.R, two_pass ? c->d_op : nullptr,
+    e = launch_f8_prep(c->L.s, d_in, T_blk, T_run, c->L.T_pad * c->L.K_batch, 0, c->L.R_buf, two_pass ? c->d_op : nullptr,
                        c->d_soff,
                        c->d_soff_auto, st);
     timer_end(c, CORR_KERNEL_UNPACK, st, tb);
@@ -361,7 +364,7 @@ int ensure_operand_scratch(corr_ctx* c) {
   cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_buf_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
   std::string err;
-  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
+  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
     cudaFree(c->d_op);
     c->d_op = nullptr;
     return fail(CORR_ERR_CUDA, err);
@@ -385,7 +388,7 @@ int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cu
     const int nb = (n - b0) < K ? (n - b0) : K;
     for (int i = 0; i < nb; ++i) {
       const bool tb = timer_begin(c, CORR_KERNEL_UNPACK, st);
-      const cudaError_t e = launch_f8_prep(c->L.s, blocks[b0 + i], T_blk, T_pad, T_span, i * T_pad, c->L.R, c->d_op,
+      const cudaError_t e = launch_f8_prep(c->L.s, blocks[b0 + i], T_blk, T_pad, T_span, i * T_pad, c->L.R_buf, c->d_op,
                                            c->d_soff, c->d_soff_auto, st);
       timer_end(c, CORR_KERNEL_UNPACK, st, tb);
       if (e != cudaSuccess) return cuda_fail(e, "batch operand build");
@@ -948,7 +951,7 @@ int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
   for (int i = 0; i < g->n; ++i) {
     corr_ctx* c = g->ctx[i];
     bool tb = timer_begin(c0, CORR_KERNEL_UNPACK, st);
-    cudaError_t e = launch_f8_prep(c->L.s, in[i], c->L.s.T, T_pad, c->L.T_pad * c->L.K_batch, 0, c->L.R, c->d_op,
+    cudaError_t e = launch_f8_prep(c->L.s, in[i], c->L.s.T, T_pad, c->L.T_pad * c->L.K_batch, 0, c->L.R_buf, c->d_op,
                                    c->d_soff, c->d_soff_auto, st);
     timer_end(c0, CORR_KERNEL_UNPACK, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "group operand build");

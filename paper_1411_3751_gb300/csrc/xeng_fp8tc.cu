@@ -27,9 +27,11 @@ constexpr int EPI_THREADS = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
 // Operand build + offset sums, one pass over the input (the paper's CPU "unpack" stage, Sec. 2.4,
-// done on the GPU). A unit = 16 inputs (32 operand rows) of one (f, t). Lane l of a warp takes unit
-// 8 blockIdx.x + (l % 8) at time offset l / 8, so a warp reads 8 units (128 inputs) of 4 samples and
-// the 8 warps of a block cover 32 samples per step; blockIdx.z splits the time range.
+// done on the GPU). A unit = 16 inputs (32 operand rows) of one channel; units are numbered across
+// channels, u = f G + g (G units per channel), so that small arrays still fill every lane. Lane l of a
+// warp takes unit 8 blockIdx.x + (l % 8) at time offset l / 8, so a warp reads 8 units (128 inputs,
+// contiguous in [t][C][N] when N % 16 == 0) of 4 samples and the 8 warps of a block cover 32 samples
+// per step; blockIdx.z splits the time range.
 //  * op (if not null): op[f][t_base + t][r] for t < T_run (zero rows for t >= T and inputs >= N);
 //  * s1, s2 (if not null): per-input offset sums sum_t (x + 8 + 8i) over t < T, added to both
 //    (the cross-cadence and the total-power-cadence copies). Per-thread sums live in 16-bit lanes of
@@ -45,8 +47,10 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   const int G = R / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tl = lane >> 3, us = lane & 7;
-  const int g = 8 * blockIdx.x + us;
-  const int f = blockIdx.y;
+  const long long unit = 8LL * blockIdx.x + us;  // flattened unit
+  const bool unit_ok = unit < (long long)C * G;
+  const int f = unit_ok ? (int)(unit / G) : 0;
+  const int g = unit_ok ? (int)(unit - (long long)f * G) : G;
   const int t_begin = blockIdx.z * rows_per_split;
   const int t_end = min(T_run, t_begin + rows_per_split);
   const int n0 = 16 * g;
@@ -54,7 +58,7 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   // packed 16-bit lane sums: [word k][even / odd byte], for Re and Im
   uint32_t sre[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
   uint32_t sim[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
-  if (g < G) {
+  if (unit_ok) {
     // 8 samples per thread per iteration, all loads issued before any conversion
     constexpr int U = 8;
     for (int t0 = t_begin + 4 * warp + tl; t0 < t_end; t0 += 32 * U) {
@@ -128,14 +132,15 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   __syncthreads();
   // thread i: unit i / 32, value i % 32
   const int uu = threadIdx.x >> 5, j = threadIdx.x & 31;
-  const int gg = 8 * blockIdx.x + uu;
-  const int n = 16 * gg + (j >> 1);
-  if (gg < G && n < N) {
+  const long long ug = 8LL * blockIdx.x + uu;
+  const int fu = (int)(ug / G), gu = (int)(ug - (long long)(ug / G) * G);
+  const int n = 16 * gu + (j >> 1);
+  if (ug < (long long)C * G && n < N) {
     long long sum = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) sum += part[w][uu][j];
     if (sum != 0) {
-      const long long idx = ((long long)f * N + n) * 2 + (j & 1);
+      const long long idx = ((long long)fu * N + n) * 2 + (j & 1);
       if (s1) atomicAdd(reinterpret_cast<unsigned long long*>(s1 + idx), (unsigned long long)sum);
       if (s2) atomicAdd(reinterpret_cast<unsigned long long*>(s2 + idx), (unsigned long long)sum);
     }
@@ -326,10 +331,11 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
   // time split: at most PREP_ROWS_PER_THREAD_MAX samples per thread (each thread takes one of 32)
   int split = 1;
   while ((long long)(T_run + split - 1) / split > 32LL * PREP_ROWS_PER_THREAD_MAX) split *= 2;
-  while ((long long)((G + 7) / 8) * s.C * split < 4 * 152 && T_run / (split * 2) >= 256) split *= 2;
+  const long long units = (long long)G * s.C;
+  while ((units + 7) / 8 * split < 4 * 152 && T_run / (split * 2) >= 256) split *= 2;
   const int rows = (int)round_up((T_run + split - 1) / split, 32);
   split = (T_run + rows - 1) / rows;
-  dim3 grid((G + 7) / 8, s.C, split);
+  dim3 grid((unsigned)((units + 7) / 8), 1, split);
   const bool vec = (s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
   f8_prep_kernel<<<grid, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, t_base, R, rows, vec, d_op, d_s1,
                                        d_s2);

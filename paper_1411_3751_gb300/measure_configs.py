@@ -3,6 +3,9 @@
 * tiny: 32 inputs x 8 channels x 1024 samples (uniform components), each arithmetic path; a launch-
   bound case (the FP32 path is the paper's arithmetic);
 
+* small: 32 and 64 inputs (LWA1's 64-input system) x 2400 channels x 4 blocks of 8192 samples, FP8
+  tensor path: Tera-CMAC/s and the HBM traffic of the two passes (input read once, operand written
+  and read back) against the measured copy bandwidth, the bound for these small arrays;
 * precision: 512 inputs x 256 channels x 65536 samples with saturation-heavy segments; X-engine time
   with in-chip partial sums flushed to int64 every 4096 / 16384 / 65536 samples on the FP8 tcgen05
   path and every 16384 / 65536 samples on the int8 mma.sync path (the flush overhead is the
@@ -20,7 +23,7 @@
 * fastdump: the 512-input x 2400-channel stream at the paper's minimum dump time (0.33 s = 8000
   samples, float32 visibilities) with 1 s total power of ten outrigger stations (selective dumps).
 
-    python -m paper_1411_3751_gb300.measure_configs [--only tiny|precision|group|stream|fastdump|requant|pfb]
+    python -m paper_1411_3751_gb300.measure_configs [--only tiny|small|precision|group|stream|fastdump|requant|pfb]
 """
 from __future__ import annotations
 
@@ -52,6 +55,39 @@ def tiny(corr, synth, torch, reps=200):
             ms = e0.elapsed_time(e1) / reps
         out[path] = {"ms_per_block": ms, "tcmac_s": _useful(N, C, T) / (ms / 1e3) / 1e12,
                      "real_time_factor": (T / 24000.0) / (ms / 1e3)}
+    return out
+
+
+def small(corr, synth, torch, reps=5, path="fp8tc"):
+    import json as _json
+
+    try:
+        hbm = float(_json.load(open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                 "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        hbm = 6800.0
+    out = {"config": "small: N=32 and 64, C=2400, 4 x 8192 samples, %s" % path, "hbm_gbs_peak": hbm}
+    T, C, B, npol = 8192, 2400, 4, 2
+    for N in (32, 64):
+        blocks = [synth.generate_device(synth.Spec(kind="gauss_tone", seed=0x14113751 + 60 + b), T, C, N)
+                  for b in range(B)]
+        with corr.Correlator(N, C, T, npol, path=path) as xc:
+            xc.accumulate_batch(blocks)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                xc.accumulate_batch(blocks)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        r_buf = ((2 * N + 31) // 32) * 32
+        samples = T * B * C
+        moved = samples * N + 2 * samples * r_buf  # input once, operand written and read back
+        out[str(N)] = {"ms_per_step": ms, "tcmac_s": _useful(N, C, T * B) / (ms / 1e3) / 1e12,
+                       "hbm_gbs": moved / (ms / 1e3) / 1e9, "hbm_frac": moved / (ms / 1e3) / 1e9 / hbm,
+                       "real_time_factor": (T * B / 24000.0) / (ms / 1e3)}
+        del blocks
     return out
 
 
@@ -216,10 +252,14 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_1411_3751_gb300 import corr, synth
 
-    todo = [a.only] if a.only else ["tiny", "precision", "group", "stream", "fastdump", "requant", "pfb"]
+    todo = [a.only] if a.only else ["tiny", "small", "precision", "group", "stream", "fastdump", "requant", "pfb"]
     for name in todo:
         if name == "tiny":
             r = tiny(corr, synth, torch)
+        elif name == "small":
+            r = small(corr, synth, torch)
+            print(json.dumps({"measure": name, **r}))
+            r = small(corr, synth, torch, path="fp8tc_fused")
         elif name == "precision":
             r = precision(corr, synth, torch)
         elif name == "group":

@@ -314,3 +314,21 @@ def test_full_size_512_inputs_128_channels(env, path):
     assert np.array_equal(cross[:, diag, 0, 0], autos[:, 0::2]) and np.array_equal(cross[:, diag, 3, 0], autos[:, 1::2])
     assert np.array_equal(cross[:, diag, 2, 0], cross[:, diag, 1, 0])
     assert np.array_equal(cross[:, diag, 2, 1], -cross[:, diag, 1, 1])
+    # 4) statistical sanity (not parity): every input carries the common tone A exp(i 2 pi (t + k_n) / 1024)
+    #    with its seeded phase k_n, so V_mn / T ~ g A^2 exp(i 2 pi (k_m - k_n) / 1024) with a quantisation
+    #    gain g near 1. Noise of one cell's mean: ~ 2 sigma^2 / sqrt(T) = 0.035 against A^2 = 1.39, i.e.
+    #    ~0.025 rad of phase; the bounds below are about 6 sigma.
+    ph = synth.phases_radians(spec, N)
+    a2 = spec.tone_amplitude() ** 2
+    Tt = B * T
+    for _ in range(200):
+        f = int(rng.integers(0, C))
+        sa = int(rng.integers(1, S))
+        sc = int(rng.integers(0, sa))
+        p, q = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+        i, j = 2 * sa + p, 2 * sc + q
+        v = cross[f, sa * (sa + 1) // 2 + sc, 2 * p + q]
+        z = complex(v[0], v[1]) / Tt
+        dphi = np.angle(z * np.exp(-1j * (ph[i] - ph[j])))
+        assert abs(dphi) < 0.15, (f, i, j, dphi)
+        assert 0.7 < abs(z) / a2 < 1.2, (f, i, j, abs(z) / a2)

@@ -5,10 +5,10 @@
 // block, block(i) >= block(j), so only the lower block triangle is visited) for one channel. Each
 // thread holds an 8 (i) x 8 (j) register tile of complex FP32 partial sums: per sample it reads 8 + 8
 // complex values from shared memory and issues 256 FMAs. Samples are staged 32 at a time in shared
-// memory as float2 (sign-extended nibbles); the raw bytes of the next 32 samples are loaded into
-// registers while the current ones are multiplied. Every `flush_len` samples (<= 65536) the partials,
-// exact integers of magnitude <= 128 * 65536 = 2^23, are converted to int64 and added to the
-// accumulators.
+// memory as float2 (sign-extended nibbles), in 8-value groups padded against bank conflicts; the raw
+// bytes of the next 32 samples are loaded into registers while the current ones are multiplied.
+// Every `flush_len` samples (<= 65536) the partials, exact integers of magnitude <= 128 * 65536 = 2^23,
+// are converted to int64 and added to the accumulators.
 #include "corr_internal.cuh"
 
 namespace corr {
@@ -16,6 +16,10 @@ namespace {
 
 constexpr int TB = 64, KT = kF32Kt, NT = 64;
 constexpr int U = 8;  // per-thread tile: U x U complex
+// Shared row of one sample: 8 groups of 8 complex values, each group padded by 2 complex (16 bytes), so
+// the 8 column groups a warp reads with 128-bit loads fall into 8 different bank groups.
+constexpr int GRP = U + 2, ROW = (TB / U) * GRP;
+__device__ __forceinline__ int sx(int n) { return (n / U) * GRP + n % U; }
 constexpr int WORDS = KT * 2 * (TB / 4) / NT;  // raw 4-byte words per thread per stage (16)
 
 __device__ __forceinline__ float nib(unsigned v) { return (float)(((int)(v & 0xF) ^ 8) - 8); }
@@ -38,8 +42,8 @@ __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict
                                                        long long Bs, int flush_len, const int2* __restrict__ tiles,
                                                        bool vec, long long* __restrict__ cross,
                                                        long long* __restrict__ autos) {
-  __shared__ __align__(16) float2 xi_s[KT][TB];
-  __shared__ __align__(16) float2 xj_s[KT][TB];
+  __shared__ __align__(16) float2 xi_s[KT][ROW];
+  __shared__ __align__(16) float2 xj_s[KT][ROW];
   const int2 tb = tiles[blockIdx.x];
   const int f = blockIdx.y;
   const int i0 = tb.x * TB, j0 = tb.y * TB;
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict
     for (int q = 0; q < WORDS; ++q) {
       const int e = tid + NT * (q & 7);
       const int tt = e >> 4, w = e & 15;
-      float2* dst = (q < 8 ? &xi_s[tt][4 * w] : &xj_s[tt][4 * w]);
+      float2* dst = (q < 8 ? &xi_s[tt][sx(4 * w)] : &xj_s[tt][sx(4 * w)]);
       const uint32_t v = raw[q];
       const float4 lo = make_float4(nib(v >> 4), nib(v), nib(v >> 12), nib(v >> 8));
       const float4 hi = make_float4(nib(v >> 20), nib(v >> 16), nib(v >> 28), nib(v >> 24));
@@ -88,8 +92,8 @@ __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict
 #pragma unroll 2
     for (int tt = 0; tt < KT; ++tt) {
       float2 a[U], b[U];
-      const float4* pa = reinterpret_cast<const float4*>(&xi_s[tt][ig * U]);
-      const float4* pb = reinterpret_cast<const float4*>(&xj_s[tt][jg * U]);
+      const float4* pa = reinterpret_cast<const float4*>(&xi_s[tt][ig * GRP]);
+      const float4* pb = reinterpret_cast<const float4*>(&xj_s[tt][jg * GRP]);
 #pragma unroll
       for (int h = 0; h < U / 2; ++h) {
         const float4 qa = pa[h], qb = pb[h];

@@ -132,6 +132,9 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[a][b][e] = 0;
 
+  // on a diagonal tile, warps whose inputs j all lie above their inputs i hold no stored pair: they
+  // stage samples and keep the barriers but issue no MMAs
+  const bool above = tb.x == tb.y && wn * 16 >= wm * 32 + 32;
   const int n_kt = (T + KT - 1) / KT;
   load_tile(0);
   store_tile(0);
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(NT, 2)
     const int lr = lane & 7, lm = lane >> 3;
 #pragma unroll
     for (int ks = 0; ks < KT / 32; ++ks) {
+      if (above) break;
       uint32_t b[4][2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {  // n8 tiles 2h, 2h+1 of this warp

@@ -156,6 +156,15 @@ def cpu_baseline(seconds_target=15.0):
     t0 = time.perf_counter()
     oracle.correlate(x, N_POL, threads=1)
     per_cmac = (time.perf_counter() - t0) / useful_cmacs(N_IN, 1, 1024)
+    # one thread on one channel, about 2 s
+    T1 = int(2.0 / (per_cmac * useful_cmacs(N_IN, 1, 1))) if per_cmac > 0 else 1024
+    T1 = max(256, min(T_BLOCK, (T1 // 256) * 256))
+    x = synth.generate_host(spec, T1, 1, N_IN)
+    t0 = time.perf_counter()
+    oracle.correlate(x, N_POL, threads=1)
+    dt1 = time.perf_counter() - t0
+    single = {"value": useful_cmacs(N_IN, 1, T1) / dt1 / 1e12, "cores": 1,
+              "sample": "1 channel x %d samples x %d inputs, %.1f s" % (T1, N_IN, dt1)}
     chans = cores
     T = int(seconds_target / (per_cmac * useful_cmacs(N_IN, 1, 1)) / 1.0) if per_cmac > 0 else 1024
     T = max(256, min(T_BLOCK, (T // 256) * 256))
@@ -167,7 +176,7 @@ def cpu_baseline(seconds_target=15.0):
     return {"value": cm / dt / 1e12, "unit": "Tera-CMAC/s", "cores": cores, "kind": "oracle",
             "sample": "%d channels x %d samples x %d inputs (of 128 x 131072 x 512), %.1f s, threads across channels"
                       % (chans, T, N_IN, dt),
-            "real_time_factor": (T / CHANNEL_RATE_HZ) / dt * (chans / N_CHAN)}
+            "real_time_factor": (T / CHANNEL_RATE_HZ) / dt * (chans / N_CHAN), "single_thread": single}
 
 
 def run_reference(args):

@@ -148,39 +148,72 @@ __device__ __forceinline__ void split_store(const float2* z, float2* __restrict_
   }
 }
 
+// 8 samples of one frame at p (8-byte aligned when vec8, else 4-byte aligned), as two words.
+__device__ __forceinline__ int2 load8(const int8_t* __restrict__ p, bool vec8) {
+  if (vec8) return __ldg(reinterpret_cast<const int2*>(p));
+  return make_int2(__ldg(reinterpret_cast<const int*>(p)), __ldg(reinterpret_cast<const int*>(p) + 1));
+}
+__device__ __forceinline__ int sbyte(int2 w, int k) {  // signed byte k (0..7) of w
+  const int v = k < 4 ? w.x : w.y;
+  return (int)(int8_t)(uint8_t)((unsigned)v >> (8 * (k & 3)));
+}
+__device__ __forceinline__ void fir_tap(int (&y)[8], const int4& c0, const int4& c1, int2 xs) {
+  y[0] += c0.x * sbyte(xs, 0);
+  y[1] += c0.y * sbyte(xs, 1);
+  y[2] += c0.z * sbyte(xs, 2);
+  y[3] += c0.w * sbyte(xs, 3);
+  y[4] += c1.x * sbyte(xs, 4);
+  y[5] += c1.y * sbyte(xs, 5);
+  y[6] += c1.z * sbyte(xs, 6);
+  y[7] += c1.w * sbyte(xs, 7);
+}
+
 // One CTA per (input, pair of spectra t0, t0 + 1): the FIR of both spectra shares each coefficient
-// load (frames t0 .. t0 + P), then each spectrum is transformed in its own shared buffer.
-__global__ void __launch_bounds__(PFB_NT) pfb_kernel(const int8_t* __restrict__ adc, long long stride, int T,
-                                                     int P, const int* __restrict__ h, float2* __restrict__ out) {
+// load and each frame load (frames t0 .. t0 + P), then each spectrum is transformed in its own shared
+// buffer. PT > 0 fixes the tap count at compile time (all loads of a step issued together); PT == 0
+// takes it from P.
+template <int PT>
+__global__ void __launch_bounds__(PFB_NT, 3) pfb_kernel(const int8_t* __restrict__ adc, long long stride, int T,
+                                                        int P, bool vec8, const int* __restrict__ h,
+                                                        float2* __restrict__ out) {
   extern __shared__ float2 zs[];  // PFB_SPB buffers of PFB_ZLEN
   const int t0 = blockIdx.x * PFB_SPB, n = blockIdx.y, tid = threadIdx.x;
   const int ns = T - t0 < PFB_SPB ? T - t0 : PFB_SPB;
   const int8_t* x = adc + (size_t)n * stride + (size_t)t0 * PFB_M;
-  // FIR: thread handles samples m = 4 tid + 1024 j (j < 8), four at a time, for both spectra
+  // FIR: thread handles samples m = 8 tid + 2048 j .. + 7 (j < 4), for both spectra
 #pragma unroll 1
-  for (int j = 0; j < PFB_M / (4 * PFB_NT); ++j) {
-    const int m = 4 * tid + 1024 * j;
-    int y[PFB_SPB][4];
+  for (int j = 0; j < PFB_M / (8 * PFB_NT); ++j) {
+    const int m = 8 * tid + 8 * PFB_NT * j;
+    int y[PFB_SPB][8];
 #pragma unroll
-    for (int s = 0; s < PFB_SPB; ++s) y[s][0] = y[s][1] = y[s][2] = y[s][3] = 0;
-    for (int p = 0; p < P; ++p) {
-      const int4 hs = *reinterpret_cast<const int4*>(h + p * PFB_M + m);
+    for (int s = 0; s < PFB_SPB; ++s)
 #pragma unroll
-      for (int s = 0; s < PFB_SPB; ++s) {
-        if (s < ns) {
-          const char4 xs = *reinterpret_cast<const char4*>(x + (size_t)(p + s) * PFB_M + m);
-          y[s][0] += hs.x * xs.x;
-          y[s][1] += hs.y * xs.y;
-          y[s][2] += hs.z * xs.z;
-          y[s][3] += hs.w * xs.w;
-        }
+      for (int k = 0; k < 8; ++k) y[s][k] = 0;
+    if (PT > 0) {
+      int2 fr[PT + 1];  // frames t0 .. t0 + PT at m
+#pragma unroll
+      for (int q = 0; q <= PT; ++q) fr[q] = q < PT || ns > 1 ? load8(x + (size_t)q * PFB_M + m, vec8) : make_int2(0, 0);
+#pragma unroll
+      for (int p = 0; p < PT; ++p) {
+        const int4* hp = reinterpret_cast<const int4*>(h + p * PFB_M + m);
+        const int4 c0 = __ldg(hp), c1 = __ldg(hp + 1);
+        fir_tap(y[0], c0, c1, fr[p]);
+        fir_tap(y[1], c0, c1, fr[p + 1]);
+      }
+    } else {
+#pragma unroll 2
+      for (int p = 0; p < P; ++p) {
+        const int4* hp = reinterpret_cast<const int4*>(h + p * PFB_M + m);
+        const int4 c0 = __ldg(hp), c1 = __ldg(hp + 1);
+        fir_tap(y[0], c0, c1, load8(x + (size_t)p * PFB_M + m, vec8));
+        if (ns > 1) fir_tap(y[1], c0, c1, load8(x + (size_t)(p + 1) * PFB_M + m, vec8));
       }
     }
 #pragma unroll
-    for (int s = 0; s < PFB_SPB; ++s) {
-      zs[s * PFB_ZLEN + sidx(m / 2)] = make_float2((float)y[s][0], (float)y[s][1]);
-      zs[s * PFB_ZLEN + sidx(m / 2 + 1)] = make_float2((float)y[s][2], (float)y[s][3]);
-    }
+    for (int s = 0; s < PFB_SPB; ++s)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        zs[s * PFB_ZLEN + sidx(m / 2 + q)] = make_float2((float)y[s][2 * q], (float)y[s][2 * q + 1]);
   }
   __syncthreads();
   for (int s = 0; s < ns; ++s) {
@@ -218,10 +251,17 @@ cudaError_t launch_pfb(const int8_t* d_adc, long long stride, int N, int T, int 
   if (e == cudaSuccess) e = ensure_twiddles(dev);
   if (e != cudaSuccess) return e;
   constexpr int smem = PFB_SPB * PFB_ZLEN * (int)sizeof(float2);
-  e = set_smem_limit(reinterpret_cast<const void*>(pfb_kernel), smem);
-  if (e != cudaSuccess) return e;
-  pfb_kernel<<<dim3((unsigned)((T + PFB_SPB - 1) / PFB_SPB), (unsigned)N), PFB_NT, smem, st>>>(d_adc, stride, T, P,
-                                                                                              d_h, d_out);
+  const bool vec8 = ((reinterpret_cast<uintptr_t>(d_adc) | (uintptr_t)stride) & 7) == 0;
+  const dim3 grid((unsigned)((T + PFB_SPB - 1) / PFB_SPB), (unsigned)N);
+  if (P == 4) {
+    e = set_smem_limit(reinterpret_cast<const void*>(pfb_kernel<4>), smem);
+    if (e != cudaSuccess) return e;
+    pfb_kernel<4><<<grid, PFB_NT, smem, st>>>(d_adc, stride, T, P, vec8, d_h, d_out);
+  } else {
+    e = set_smem_limit(reinterpret_cast<const void*>(pfb_kernel<0>), smem);
+    if (e != cudaSuccess) return e;
+    pfb_kernel<0><<<grid, PFB_NT, smem, st>>>(d_adc, stride, T, P, vec8, d_h, d_out);
+  }
   return cudaGetLastError();
 }
 

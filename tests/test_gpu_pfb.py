@@ -54,13 +54,15 @@ def test_pfb_random_adc(env, n_taps):
     _check(X, adc, n_taps)
 
 
-def test_pfb_extreme_samples_and_strided_inputs(env):
-    """Full-scale samples (the int32 FIR sums reach 2^26) and inputs at a row stride beyond the data."""
+@pytest.mark.parametrize("pad", [4096, 4])
+def test_pfb_extreme_samples_and_strided_inputs(env, pad):
+    """Full-scale samples (the int32 FIR sums reach 2^26) and inputs at a row stride beyond the data
+    (pad 4: rows only 4-byte aligned, the narrow-load variant)."""
     corr, torch = env
     rng = np.random.default_rng(5)
-    N, T, P = 3, 4, 4
+    N, T, P = 3, 5, 4
     S = (T + P - 1) * M
-    adc = rng.choice(np.array([-128, 127], dtype=np.int8), size=(N, S + 4096))
+    adc = rng.choice(np.array([-128, 127], dtype=np.int8), size=(N, S + pad))
     d = torch.from_numpy(adc).cuda()
     coeffs = torch.from_numpy(corr.corr_pfb_coeffs(M, P)).cuda()
     out = torch.empty((N, T, M // 2, 2), dtype=torch.float32, device="cuda")

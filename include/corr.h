@@ -24,7 +24,8 @@
  * Autos    [C][N]: sum_t |x_n(t)|^2 (real).
  * Formats  CORR_FMT_CI64: int64 (re, im) / int64 autos, the exact sums.
  *          CORR_FMT_CF32: float32, each int64 rounded to nearest.
- *          CORR_FMT_CF32_NORM: float32 of (double)sum / (double)n_samples (the time average, Sec. 2.5).
+ *          CORR_FMT_CF32_NORM: float32 of (double)sum / (double)n_samples (the time average, Sec. 2.5);
+ *          0 where nothing has been accumulated since the last reset.
  * Streams  every call that takes a `cuda_stream` (a cudaStream_t, NULL = legacy default stream)
  *          only enqueues work on it and returns; work is ordered by the stream.
  * Errors   functions return CORR_OK (0) or a negative corr_status; corr_last_error() gives a

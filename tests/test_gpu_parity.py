@@ -71,6 +71,38 @@ def test_ragged_shapes(env, path, shape):
     _check(env, host, npol, path)
 
 
+@pytest.mark.parametrize("path", PATHS)
+def test_maximum_channel_count(env, path):
+    """C = 65535, the largest channel count the ABI accepts (one grid dimension per channel on the
+    CUDA-core and int8 paths, 65535 work items on the tensor path), with 2 inputs and 3 samples."""
+    _, synth, _ = env
+    host = synth.generate_host(synth.Spec(kind="uniform", seed=65535), 3, 65535, 2)
+    _check(env, host, 2, path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_empty_context_and_empty_batch(env, path):
+    """Nothing accumulated (a fresh context, then an empty batch): every dump format gives zeros,
+    the normalised format included, and the sample counters stay at 0; then one real block."""
+    corr, synth, torch = env
+    N, C, T, npol = 40, 3, 200, 2
+    with corr.Correlator(N, C, T, npol, path=path) as xc:
+        xc.accumulate_batch([])
+        for what in (corr.CORR_WHAT_CROSS, corr.CORR_WHAT_AUTO):
+            assert xc.samples(what) == 0
+            for fmt in (corr.CORR_FMT_CI64, corr.CORR_FMT_CF32, corr.CORR_FMT_CF32_NORM):
+                out = xc.dump(what, fmt=fmt)
+                xc.sync()
+                assert out.shape[0] == C and not torch.any(out != 0).item(), (what, fmt)
+        host = synth.generate_host(synth.Spec(kind="gauss_tone", seed=77), T, C, N)
+        xc.accumulate(torch.from_numpy(host).cuda())
+        cross = xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy()
+        autos = xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy()
+        xc.sync()
+    want_c, want_a = oracle.correlate(host, npol)
+    assert np.array_equal(cross, want_c) and np.array_equal(autos, want_a)
+
+
 @pytest.mark.parametrize("path", ["fp32", "i8mma", "fp8tc"])
 def test_large_array_2048_inputs(env, path):
     """N = 2048 (1024 dual-pol stations, four times the paper's array): many tiles per channel and

@@ -86,13 +86,19 @@ constexpr int PFB_ZLEN = PFB_H + PFB_H / 16;  // padded complex buffer per spect
 __device__ __forceinline__ void fft4096(float2* z, int tid) {
 #pragma unroll 1
   for (int Ns = 1, tw = PFB_H / 16; Ns < PFB_H; Ns *= 16, tw /= 16) {
+    const int k = tid & (Ns - 1);
+    const int e = k * tw;  // < 4096 / 16; the table loads go out before the shared-memory loads
+    float2 w1 = make_float2(1.f, 0.f), w4 = w1, w8 = w1, w12 = w1;
+    if (Ns > 1) {
+      w1 = g_w4096[e];
+      w4 = g_w4096[4 * e];
+      w8 = g_w4096[8 * e];
+      w12 = g_w4096[12 * e];
+    }
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = z[sidx(tid + r * (PFB_H / 16))];
-    const int k = tid & (Ns - 1);
     if (Ns > 1) {
-      const int e = k * tw;  // < 4096 / 16
-      const float2 w1 = g_w4096[e], w4 = g_w4096[4 * e], w8 = g_w4096[8 * e], w12 = g_w4096[12 * e];
       const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
       v[1] = cmul(v[1], w1);
       v[2] = cmul(v[2], w2);
@@ -127,9 +133,18 @@ __device__ __forceinline__ void split_store(const float2* z, float2* __restrict_
     const float2 zh = z[sidx(PFB_H / 2)];              // k = 2048: X = conj(Z[2048]) (W^2048 = -i)
     o[PFB_H / 2] = make_float2(zh.x * PFB_SCALE, -zh.y * PFB_SCALE);
   }
-  for (int k = 1 + tid; k < PFB_H / 2; k += PFB_NT) {
+  float2 wk[PFB_H / 2 / PFB_NT];  // this thread's split twiddles, loaded together
+#pragma unroll
+  for (int q = 0; q < PFB_H / 2 / PFB_NT; ++q) {
+    const int k = 1 + tid + q * PFB_NT;
+    wk[q] = k < PFB_H / 2 ? g_w8192[k] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < PFB_H / 2 / PFB_NT; ++q) {
+    const int k = 1 + tid + q * PFB_NT;
+    if (k >= PFB_H / 2) break;
     const float2 a = z[sidx(k)], b = z[sidx(PFB_H - k)];
-    const float2 w = g_w8192[k];
+    const float2 w = wk[q];
     const float2 wm = make_float2(-w.x, w.y);  // W^(4096 - k) = -conj(W^k)
     // k: E = (a + conj b) / 2, O = (a - conj b) / 2, X[k] = E - i W^k O
     {

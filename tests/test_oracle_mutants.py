@@ -1,10 +1,17 @@
-"""The pins must catch plausible mistakes in the oracle: each mutant below is a copy of
-oracle/corr_oracle.c with one deliberate error, compiled with gcc into a temporary library (the
-committed oracle is untouched). With the mutant in place of the oracle, the pins of
-test_oracle_pins.py are run again; every mutant must fail at least two of them."""
+"""The pins must catch plausible mistakes in the oracle.
+
+* C mutants: a copy of oracle/corr_oracle.c with one deliberate error, compiled with gcc into a
+  temporary library; every mutant must fail at least two of the correlation pins.
+* numpy mutants: a copy of oracle/oracle.py with one deliberate error in the requantiser, the PFB,
+  the station selection, the dump formats or the sample unpacking, executed as a separate module
+  whose functions replace the oracle's; every mutant must fail at least one pin (an assertion or an
+  error).
+
+The committed oracle is never modified; the mutants exist only for the duration of a test."""
 import ctypes
 import os
 import subprocess
+import types
 
 import pytest
 
@@ -12,6 +19,7 @@ import tests.test_oracle_pins as pins
 from oracle import oracle
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "corr_oracle.c")
+PY_SRC = os.path.join(os.path.dirname(SRC), "oracle.py")
 
 MUTANTS = {
     "conjugate on the wrong side": (
@@ -76,3 +84,94 @@ def test_pins_catch_the_mutant(tmp_path, monkeypatch, name):
         except AssertionError:
             caught.append(label)
     assert len(caught) >= 2, "mutant '%s' caught only by %s" % (name, caught)
+
+
+NP_MUTANTS = {
+    "requantize: ties rounded away from zero": (
+        "r = np.rint(xf)",
+        "r = np.trunc(xf + np.copysign(np.float32(0.5), xf))"),
+    "requantize: gain product in double precision": (
+        "xf = (sel.astype(np.float32) * g).astype(np.float32)",
+        "xf = sel.astype(np.float64) * np.asarray(g, dtype=np.float64)"),
+    "requantize: Re and Im nibbles swapped": (
+        "(((r[..., 0] & 0xF) << 4) | (r[..., 1] & 0xF))",
+        "(((r[..., 1] & 0xF) << 4) | (r[..., 0] & 0xF))"),
+    "requantize: clipped at +8": (
+        "np.clip(r, lo, 7.0)",
+        "np.clip(r, lo, 8.0)"),
+    "requantize: corner turn to [C][T][N]": (
+        "packed.transpose(1, 2, 0)",
+        "packed.transpose(2, 1, 0)"),
+    "pfb_coeffs: Hann instead of Hamming window": (
+        "0.54 - 0.46 * np.cos",
+        "0.5 - 0.5 * np.cos"),
+    "pfb_coeffs: sinc twice as wide": (
+        "np.sinc((j - 0.5 * (L - 1)) / n_fft)",
+        "np.sinc((j - 0.5 * (L - 1)) / (2 * n_fft))"),
+    "pfb_fir: taps in reverse order": (
+        "h[p * n_fft:(p + 1) * n_fft]",
+        "h[(n_taps - 1 - p) * n_fft:(n_taps - p) * n_fft]"),
+    "pfb: conjugated DFT": (
+        "np.fft.rfft(y.astype(np.float64), axis=-1)",
+        "np.conj(np.fft.rfft(y.astype(np.float64), axis=-1))"),
+    "pfb: 1 / M scale dropped": (
+        "[..., :n_fft // 2] / n_fft",
+        "[..., :n_fft // 2]"),
+    "station_cross: pair transposed": (
+        "cl.append((f, st[k] * n_pol + p, st[l] * n_pol + q))",
+        "cl.append((f, st[l] * n_pol + q, st[k] * n_pol + p))"),
+    "to_format: normalised by n - 1": (
+        "/ float(n_samples)",
+        "/ float(max(n_samples - 1, 1))"),
+    "unpack: sign extension off by one": (
+        "re = np.where(re >= 8, re - 16, re)",
+        "re = np.where(re > 8, re - 16, re)"),
+}
+
+NP_FUNCS = ("requantize", "pfb_coeffs", "pfb_fir", "pfb", "station_cross", "station_autos", "to_format", "unpack",
+            "pack")
+
+NP_PIN_CALLS = [
+    ("brute force n_pol=2", lambda: pins.test_brute_force_every_cell(2, (33, 4, 6))),
+    ("pack / unpack", pins.test_pack_unpack_roundtrip_and_range),
+    ("dump formats", pins.test_dump_formats),
+    ("station subset n_pol=1", lambda: pins.test_station_subset_brute_force(1)),
+    ("station subset n_pol=2", lambda: pins.test_station_subset_brute_force(2)),
+    ("station subset of all", pins.test_station_subset_of_all_stations_is_the_full_dump),
+    ("requantize power-of-two gain", pins.test_requantize_power_of_two_gain_matches_integer_rounding),
+    ("requantize clip and specials", pins.test_requantize_identity_clip_and_specials),
+    ("requantize single-precision gain", pins.test_requantize_gain_product_is_single_precision),
+    ("requantize corner turn", pins.test_requantize_corner_turn_and_per_channel_gains),
+    ("pfb coefficients", pins.test_pfb_coeffs_shape_symmetry_and_peak),
+    ("pfb brute force", pins.test_pfb_fir_and_dft_brute_force),
+    ("pfb tone response", pins.test_pfb_channel_response_of_a_tone),
+    ("pfb linearity", pins.test_pfb_linearity),
+]
+
+
+def _mutant_module(old, new):
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, "mutation site not found or ambiguous: " + old
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = PY_SRC
+    exec(compile(src.replace(old, new), PY_SRC, "exec"), mod.__dict__)
+    return mod
+
+
+def test_unmutated_oracle_passes_every_numpy_pin():
+    for label, call in NP_PIN_CALLS:
+        call()
+
+
+@pytest.mark.parametrize("name", sorted(NP_MUTANTS))
+def test_pins_catch_the_numpy_mutant(monkeypatch, name):
+    mod = _mutant_module(*NP_MUTANTS[name])
+    for fn in NP_FUNCS:
+        monkeypatch.setattr(oracle, fn, getattr(mod, fn))
+    caught = []
+    for label, call in NP_PIN_CALLS:
+        try:
+            call()
+        except Exception:  # an assertion, or an error from a wrong shape or type
+            caught.append(label)
+    assert caught, "numpy mutant '%s' caught by no pin" % name

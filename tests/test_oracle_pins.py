@@ -344,6 +344,20 @@ def test_requantize_identity_clip_and_specials():
     np.testing.assert_array_equal(sym, [0x79, 0x07, 0x97, 0x96])
 
 
+def test_requantize_gain_product_is_single_precision():
+    """The gain product is one IEEE single-precision multiply, rounded before rint: for v = 3 and the
+    float32 gains 0x3F555556 (13981014 / 2^24) and 0x3F955555 (9786709 / 2^23) the exact products are
+    2.5 + 2^-23 and 3.5 - 2^-23, half an ulp from the half-integers, and round (ties to even) to 2.5
+    and 3.5 in float32; rint then gives 2 and 4 where the exact products would give 3 and 3."""
+    g1 = np.array([0x3F555556], dtype=np.uint32).view(np.float32)[0]
+    g2 = np.array([0x3F955555], dtype=np.uint32).view(np.float32)[0]
+    assert float(g1) == 13981014 / 2 ** 24 and float(g2) == 9786709 / 2 ** 23
+    x = np.array([[[[3, -3]]]], dtype=np.int32)
+    assert oracle.requantize(x, 0, 1, gain=g1)[0, 0, 0] == ((2 << 4) | (-2 & 0xF))   # 0x2E
+    assert oracle.requantize(x, 0, 1, gain=g2)[0, 0, 0] == ((4 << 4) | (-4 & 0xF))   # 0x4C
+    assert oracle.requantize(x.astype(np.float32), 0, 1, gains=np.array([g2], np.float32))[0, 0, 0] == 0x4C
+
+
 def test_requantize_corner_turn_and_per_channel_gains():
     rng = np.random.default_rng(8)
     N, T, F = 5, 3, 11

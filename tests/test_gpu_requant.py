@@ -58,6 +58,24 @@ def test_requantize_float32_specials_and_channel_gains(env):
     assert np.array_equal(got, oracle.requantize(x, chan0, C, gain=1.0))
 
 
+@pytest.mark.parametrize("in_type", ["int32", "float32"])
+def test_requantize_gain_product_in_single_precision(env, in_type):
+    """v = +-3 with the float32 gains 0x3F555556 and 0x3F955555: the single-precision products are
+    exactly +-2.5 and +-3.5 (the exact products are half an ulp off), so rint gives +-2 and +-4."""
+    corr, torch = env
+    gains = np.array([0x3F555556, 0x3F955555], dtype=np.uint32).view(np.float32)
+    x = np.zeros((2, 1, 2, 2), dtype=np.int32 if in_type == "int32" else np.float32)
+    x[0, 0, :] = (3, -3)
+    x[1, 0, :] = (-3, 3)
+    xd = torch.from_numpy(x).cuda()
+    got = corr.requantize(xd, 0, 2, gains=torch.from_numpy(gains).cuda()).cpu().numpy()
+    assert np.array_equal(got, oracle.requantize(x, 0, 2, gains=gains))
+    assert got[0, 0, 0] == 0x2E and got[0, 1, 0] == 0x4C and got[0, 0, 1] == 0xE2 and got[0, 1, 1] == 0xC4
+    for c, g in enumerate(gains):
+        one = corr.requantize(xd, c, 1, gain=float(g)).cpu().numpy()
+        assert np.array_equal(one[:, 0, :], got[:, c, :])
+
+
 def test_requantized_data_through_the_x_engine(env):
     """F-engine tail -> X-engine on the device: visibilities of the requantised PFB output."""
     corr, torch = env

@@ -106,6 +106,19 @@ int corr_set_path(corr_ctx* ctx, int path);
 int corr_get_path(const corr_ctx* ctx);
 
 /*
+ * corr_set_tile_plan - how the two-pass tensor path cuts the triangle a >= c of each channel
+ * (Sec. 2.5's pairwise products) into work items: 0 (default) tiles of 64 c-inputs x 128 a-inputs
+ * (64 on the diagonal); 1 tiles of 64 x 64; 2 pairs of 64-input c-blocks against 128 a-inputs, the
+ * two halves sharing one operand tile (a third fewer operand bytes per product; the pair fills both
+ * TMEM accumulators, so its drain is not overlapped with the next item). Results are identical for
+ * every plan. Waits for the device (queued launches read the current work list). CORR_ERR_ARG for
+ * another value. Group launches (corr_group_*) always use plan 0 or 1. corr_get_tile_plan returns
+ * the current plan (CORR_ERR_ARG for a NULL context).
+ */
+int corr_set_tile_plan(corr_ctx* ctx, int plan);
+int corr_get_tile_plan(const corr_ctx* ctx);
+
+/*
  * corr_set_flush_period - maximum number of samples accumulated in on-chip FP32/int32 partial sums
  * before they are added to the int64 accumulators (the paper integrates 8000-spectrum groups and
  * then sums 27 of them, Sec. 2.5; the flush cadence is this library's choice). 0 restores the

@@ -29,6 +29,8 @@ SIGNATURES = [
     ("corr_create", _c_vp, [_c_int, _c_int, _c_int, _c_int]),
     ("corr_set_path", _c_int, [_c_vp, _c_int]),
     ("corr_get_path", _c_int, [_c_vp]),
+    ("corr_set_tile_plan", _c_int, [_c_vp, _c_int]),
+    ("corr_get_tile_plan", _c_int, [_c_vp]),
     ("corr_set_flush_period", _c_int, [_c_vp, _c_int]),
     ("corr_accumulate", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_accumulate_batch", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_vp]),
@@ -103,6 +105,14 @@ def corr_set_path(ctx: int, path: int) -> int:
 
 def corr_get_path(ctx: int) -> int:
     return _check(_lib.corr_get_path(ctx), "corr_get_path")
+
+
+def corr_set_tile_plan(ctx: int, plan: int) -> int:
+    return _check(_lib.corr_set_tile_plan(ctx, plan), "corr_set_tile_plan")
+
+
+def corr_get_tile_plan(ctx: int) -> int:
+    return _check(_lib.corr_get_tile_plan(ctx), "corr_get_tile_plan")
 
 
 def corr_set_flush_period(ctx: int, n_samples: int) -> int:
@@ -334,6 +344,14 @@ class Correlator:
 
     def set_flush_period(self, n: int):
         corr_set_flush_period(self.ctx, n)
+
+    def set_tile_plan(self, plan: int):
+        """Work-item plan of the two-pass tensor path (0 default, 1, 2: c-block pairs)."""
+        corr_set_tile_plan(self.ctx, plan)
+
+    @property
+    def tile_plan(self) -> int:
+        return corr_get_tile_plan(self.ctx)
 
     @property
     def path(self) -> int:

@@ -304,13 +304,15 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
 }
 
 // Tile plan of the tensor paths: the tile list (fused path) and the channel-major work list
-// (two-pass path) for plan 0 or 1 (see f8_tile_plan).
+// (two-pass path) for plan 0, 1 or 2 (see f8_tile_plan).
 int set_tile_plan(corr_ctx* c, int plan) {
-  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan);
+  // the fused path has no wide mode: it keeps plan 0 under plan 2
+  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan == 2 ? 0 : plan);
+  const std::vector<F8Tile> tw = plan == 2 ? f8_tile_plan(c->L.s.N, c->L.R, 2) : t8;
   std::vector<WorkItem> items;
-  items.reserve((size_t)c->L.s.C * t8.size());
+  items.reserve((size_t)c->L.s.C * tw.size());
   for (int f = 0; f < c->L.s.C; ++f)
-    for (const F8Tile& t : t8) items.push_back(WorkItem{0, f, t.c0, t.a0, t.nb, 0});
+    for (const F8Tile& t : tw) items.push_back(WorkItem{0, f, t.c0, t.a0, t.nb, t.pad});
   F8Tile* d_t = nullptr;
   WorkItem* d_i = nullptr;
   if (cudaMalloc(&d_t, t8.size() * sizeof(F8Tile)) != cudaSuccess ||
@@ -350,6 +352,7 @@ XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flu
   a.T_run = T_run;
   a.flush_len = flush;
   a.err = c->d_err;
+  a.wide = c->tile_plan == 2 ? 1 : 0;
   return a;
 }
 
@@ -521,6 +524,17 @@ int corr_set_path(corr_ctx* c, int path) {
 }
 
 int corr_get_path(const corr_ctx* c) { return c ? resolved_path(c) : CORR_ERR_ARG; }
+
+int corr_set_tile_plan(corr_ctx* c, int plan) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_set_tile_plan: NULL context");
+  if (plan < 0 || plan > 2) return fail(CORR_ERR_ARG, "corr_set_tile_plan: plan must be 0, 1 or 2");
+  // the work lists are read by queued launches: replace them once those are done
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "corr_set_tile_plan: synchronize");
+  return set_tile_plan(c, plan);
+}
+
+int corr_get_tile_plan(const corr_ctx* c) { return c ? c->tile_plan : CORR_ERR_ARG; }
 
 int corr_set_flush_period(corr_ctx* c, int n) {
   if (!c) return fail(CORR_ERR_ARG, "corr_set_flush_period: NULL context");
@@ -918,7 +932,8 @@ int group_build_items(corr_group* g) {
   std::vector<WorkItem> items;
   for (int i : order) {
     corr_ctx* c = g->ctx[i];
-    const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan);
+    // group launches run the default mode: a member on plan 2 joins with plan 0
+    const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan == 2 ? 0 : c->tile_plan);
     for (int f = 0; f < c->L.s.C; ++f)
       for (const F8Tile& t : t8) items.push_back(WorkItem{i, f, t.c0, t.a0, t.nb, 0});
   }

@@ -73,6 +73,7 @@ struct XengArgs {
   int T_run;      // samples multiplied per item (multiple of kF8Kt)
   int flush_len;  // samples per in-chip partial sum
   int* err;
+  int wide;       // items are c-block pairs of tile plan 2 (see f8_tile_plan)
 };
 
 constexpr int kF8Kt = 128;             // time samples per pipeline stage
@@ -124,7 +125,10 @@ cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st);
 
 // Tile plans of the triangle (a >= c) for N inputs with R operand rows: plan 0 = a-side spans of
 // 128 inputs (N = 256 rows) with a half-width first span on odd c-blocks; plan 1 = spans of 64
-// inputs (N = 128) everywhere.
+// inputs (N = 128) everywhere; plan 2 = pairs of c-blocks (c0, c0 + 64) against a-spans of 128
+// inputs, both halves sharing the B operand (wide mode of the two-pass X-engine): nb = half 0's
+// width, pad = half 1's width | (1 << 16 when half 1 starts at the second B atom, on a diagonal
+// pair); half 1's width is 0 when c0 + 64 >= N.
 std::vector<F8Tile> f8_tile_plan(int N, int R, int plan);
 
 size_t f8_smem_bytes();

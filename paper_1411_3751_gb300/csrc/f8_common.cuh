@@ -59,8 +59,10 @@ __device__ __forceinline__ void record_error(int* err, volatile int* abort_flag,
 // a-side rows) into cross[f]. Called by a warp of lane quarter q; the warps sharing a quarter take
 // 32-column chunks first, first + stride, ... Per chunk each thread owns 8 output cells: the lane
 // holding Re c and its partner holding Im c (lane ^ 4) exchange half of their columns by shuffle,
-// and all 8 loads of the old int64 values are issued before any store.
+// and all 8 loads of the old int64 values are issued before any store. With RED the sums are added
+// by fire-and-forget 64-bit reductions instead (no load to wait for; exact in any order).
 // Diagonal cells (a == c) are also added to autos[f][a] (offset-domain total power).
+template <bool RED = false>
 __device__ __forceinline__ void drain_tile(uint32_t tacc, int q, int lane, int first, int stride, const F8Tile& tl,
                                            int f, int N, int npol, long long Bs, long long* __restrict__ cross,
                                            long long* __restrict__ autos) {
@@ -102,17 +104,31 @@ __device__ __forceinline__ void drain_tile(uint32_t tacc, int q, int lane, int f
           const long long b = (long long)sa * (sa + 1) / 2 + sc;
           cell[m] = cross + (((long long)f * Bs + b) * P + (a % npol) * npol + pc) * 2;
           valid |= 1u << m;
-          if (a == c) autos[(long long)f * N + a] += re[m];
+          if (a == c) {
+            if (RED)
+              atomicAdd(reinterpret_cast<unsigned long long*>(autos + (long long)f * N + a), (unsigned long long)(long long)re[m]);
+            else
+              autos[(long long)f * N + a] += re[m];
+          }
         }
       }
     }
-    longlong2 old[8];
+    if (RED) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) old[m] = *reinterpret_cast<const longlong2*>(cell[m]);
+      for (int m = 0; m < 8; ++m)
+        if (valid & (1u << m)) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(cell[m]), (unsigned long long)(long long)re[m]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(cell[m]) + 1, (unsigned long long)(long long)im[m]);
+        }
+    } else {
+      longlong2 old[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m)
-      if (valid & (1u << m))
-        *reinterpret_cast<longlong2*>(cell[m]) = make_longlong2(old[m].x + re[m], old[m].y + im[m]);
+      for (int m = 0; m < 8; ++m) old[m] = *reinterpret_cast<const longlong2*>(cell[m]);
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        if (valid & (1u << m))
+          *reinterpret_cast<longlong2*>(cell[m]) = make_longlong2(old[m].x + re[m], old[m].y + im[m]);
+    }
   }
 }
 

@@ -26,6 +26,14 @@ constexpr int NUM_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int EPI_THREADS = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
+// Ring of the wide mode (tile plan 2): each item is a pair of 64-input c-blocks against one a-block
+// of up to 128 inputs, both halves sharing the B operand: a stage holds A0 | A1 | B (2 atoms), 64 KB,
+// and the two M = 128 MMAs per K step write TMEM columns 0 .. 255 (half 0) and 256 .. 511 (half 1),
+// so the item uses both accumulators and is drained before the next one starts.
+constexpr int W_STAGES = 3;
+constexpr int W_STAGE_BYTES = 2 * A_BYTES + 2 * B_ATOM;
+static_assert(W_STAGES * W_STAGE_BYTES <= STAGES * STAGE_BYTES, "wide ring must fit the shared memory of the default");
+
 // Operand build + offset sums, one pass over the input (the paper's CPU "unpack" stage, Sec. 2.4,
 // done on the GPU). A unit = 16 inputs (32 operand rows) of one channel; units are numbered across
 // channels, u = f G + g (G units per channel), so that small arrays still fill every lane. Lane l of a
@@ -147,7 +155,11 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   }
 }
 
+template <bool WIDE>
 __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_constant__ XengArgs args) {
+  constexpr int RING = WIDE ? W_STAGES : STAGES;
+  constexpr int RING_BYTES = WIDE ? W_STAGE_BYTES : STAGE_BYTES;
+  constexpr int B_OFF = WIDE ? 2 * A_BYTES : A_BYTES;  // B within a stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -192,35 +204,37 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
       // ---------------- TMA producer ----------------
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t issued_phase[STAGES];
-      bool issued[STAGES];
-      for (int s = 0; s < STAGES; ++s) issued[s] = false;
+      uint32_t issued_phase[RING];
+      bool issued[RING];
+      for (int s = 0; s < RING; ++s) issued[s] = false;
       for (long long w = blockIdx.x; w < total && !*abort_flag; w += gridDim.x) {
         const WorkItem tl = items[w];
         const int f = tl.f;
         const CUtensorMap* tmap = &args.a[tl.array].tmap;
-        const uint32_t bytes = A_BYTES + (tl.nb == 256 ? B_BYTES : B_ATOM);
+        const bool a1 = WIDE && (tl.pad & 0xFFFF) != 0;  // second c-block present
+        const uint32_t bytes = A_BYTES * (a1 ? 2 : 1) + (tl.nb == 256 ? B_BYTES : B_ATOM);
         for (int ks = 0; ks < n_k; ++ks) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1, WAIT_NS)) {
             record_error(err, abort_flag, 1);
             break;
           }
-          uint8_t* a_dst = smem + stage * STAGE_BYTES;
-          uint8_t* b_dst = a_dst + A_BYTES;
+          uint8_t* a_dst = smem + stage * RING_BYTES;
+          uint8_t* b_dst = a_dst + B_OFF;
           ptx::mbar_arrive_expect_tx(&full[stage], bytes);
           ptx::tma_load_3d(a_dst, tmap, &full[stage], 2 * tl.c0, ks * KT, f);
+          if (a1) ptx::tma_load_3d(a_dst + A_BYTES, tmap, &full[stage], 2 * tl.c0 + 128, ks * KT, f);
           ptx::tma_load_3d(b_dst, tmap, &full[stage], 2 * tl.a0, ks * KT, f);
           if (tl.nb == 256) ptx::tma_load_3d(b_dst + B_ATOM, tmap, &full[stage], 2 * tl.a0 + 128, ks * KT, f);
           issued[stage] = true;
           issued_phase[stage] = phase;
-          if (++stage == STAGES) {
+          if (++stage == RING) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
       // Copies still in flight must land before the CTA exits (normally all were consumed).
-      for (int s = 0; s < STAGES; ++s)
+      for (int s = 0; s < RING; ++s)
         if (issued[s]) ptx::mbar_wait(&full[s], issued_phase[s], WAIT_NS);
     }
   } else if (warp == 1) {
@@ -236,6 +250,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
       for (long long w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
         const WorkItem tl = items[w];
         const uint32_t idesc = tl.nb == 256 ? id256 : id128;
+        // wide mode, half 1: N = nb1 columns of B starting at atom b1 (0, or 1 on a diagonal pair)
+        const int nb1 = WIDE ? (tl.pad & 0xFFFF) : 0;
+        const uint32_t idesc1 = nb1 == 256 ? id256 : id128;
+        const uint32_t b1_off = WIDE && (tl.pad >> 16) ? (uint32_t)B_ATOM : 0u;
         for (int k0 = 0; k0 < n_k && ok; k0 += chunk_k) {
           const int k1 = min(k0 + chunk_k, n_k);
           if (!ptx::mbar_wait(&tempty[acc], (use[acc] & 1) ^ 1, WAIT_NS)) {
@@ -252,8 +270,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
               break;
             }
             ptx::tc_fence_after();
-            const uint32_t a_addr = ptx::smem_u32(smem + stage * STAGE_BYTES);
-            const uint32_t b_addr = a_addr + A_BYTES;
+            const uint32_t a_addr = ptx::smem_u32(smem + stage * RING_BYTES);
+            const uint32_t b_addr = a_addr + B_OFF;
 #pragma unroll
             for (int kk = 0; kk < KT / 32; ++kk) {
               // MN-major, 128-byte swizzle: 8 samples x 128 rows per 1024-byte atom (SBO), the
@@ -261,9 +279,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
               const uint64_t ad = ptx::smem_desc(a_addr + kk * 4096, 16, 1024, 2);
               const uint64_t bd = ptx::smem_desc(b_addr + kk * 4096, B_ATOM, 1024, 2);
               ptx::mma_f8f6f4(d, ad, bd, idesc, (ks > k0 || kk > 0) ? 1u : 0u);
+              if (WIDE && nb1 > 0) {
+                const uint64_t ad1 = ptx::smem_desc(a_addr + A_BYTES + kk * 4096, 16, 1024, 2);
+                const uint64_t bd1 = ptx::smem_desc(b_addr + b1_off + kk * 4096, B_ATOM, 1024, 2);
+                ptx::mma_f8f6f4(d + ACC_COLS, ad1, bd1, idesc1, (ks > k0 || kk > 0) ? 1u : 0u);
+              }
             }
             ptx::mma_commit(&empty[stage]);
-            if (++stage == STAGES) {
+            if (++stage == RING) {
               stage = 0;
               phase ^= 1;
             }
@@ -271,7 +294,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
           if (!ok) break;
           ptx::mma_commit(&tfull[acc]);
           ++use[acc];
-          acc ^= 1;
+          if (!WIDE) acc ^= 1;  // the wide mode fills both accumulators: one handoff slot
         }
       }
       // all issued MMAs complete before TMEM is released
@@ -306,11 +329,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
           break;
         }
         ptx::tc_fence_after();
-        drain_tile(tbase + acc * ACC_COLS, q, lane, half, 2, tl, it.f, arr.N, arr.npol, arr.Bs, arr.cross, arr.autos);
+        if (!WIDE) {
+          drain_tile(tbase + acc * ACC_COLS, q, lane, half, 2, tl, it.f, arr.N, arr.npol, arr.Bs, arr.cross, arr.autos);
+        } else {
+          // warps 2-5 drain half 0 (c-block c0), warps 6-9 half 1 (c-block c0 + 64, a-inputs from
+          // a0 + 64 on a diagonal pair); one warp per TMEM lane quarter each
+          const int nb1 = it.pad & 0xFFFF;
+          if (half == 0) {
+            drain_tile<true>(tbase, q, lane, 0, 1, tl, it.f, arr.N, arr.npol, arr.Bs, arr.cross, arr.autos);
+          } else if (nb1 > 0) {
+            F8Tile t1;
+            t1.c0 = it.c0 + 64;
+            t1.a0 = it.a0 + ((it.pad >> 16) ? 64 : 0);
+            t1.nb = nb1;
+            t1.pad = 0;
+            drain_tile<true>(tbase + ACC_COLS, q, lane, 0, 1, t1, it.f, arr.N, arr.npol, arr.Bs, arr.cross, arr.autos);
+          }
+        }
         ptx::tc_fence_before();
         ptx::mbar_arrive(&tempty[acc]);
         ++use[acc];
-        acc ^= 1;
+        if (!WIDE) acc ^= 1;
       }
     }
   }
@@ -344,17 +383,42 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
 
 cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st) {
   {
-    const cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel), SMEM_BYTES);
+    cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<false>), SMEM_BYTES);
+    if (e == cudaSuccess) e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<true>), SMEM_BYTES);
     if (e != cudaSuccess) return e;
   }
   if (args.n_items == 0 || args.T_run == 0) return cudaSuccess;
   const int grid = (int)(args.n_items < num_sms ? args.n_items : num_sms);
-  f8_xeng_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
+  if (args.wide)
+    f8_xeng_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
+  else
+    f8_xeng_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
   return cudaGetLastError();
 }
 
 std::vector<F8Tile> f8_tile_plan(int N, int R, int plan) {
   std::vector<F8Tile> t;
+  if (plan == 2) {
+    for (int c0 = 0; c0 < N; c0 += 128)
+      for (int a0 = c0; a0 < N; a0 += 128) {
+        F8Tile x;
+        x.c0 = c0;
+        x.a0 = a0;
+        x.nb = R - 2 * a0 < 256 ? R - 2 * a0 : 256;
+        int nb1 = 0, hi = 0;
+        if (c0 + 64 < N) {
+          if (a0 == c0) {  // half 1 needs only the a-inputs from a0 + 64: the second B atom
+            hi = 1;
+            nb1 = 2 * a0 + 256 <= R ? 128 : 0;
+          } else {
+            nb1 = x.nb;
+          }
+        }
+        x.pad = nb1 | (hi << 16);
+        t.push_back(x);
+      }
+    return t;
+  }
   const int ncb = (N + 63) / 64;
   for (int cb = 0; cb < ncb; ++cb) {
     int a0 = 64 * cb;

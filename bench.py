@@ -324,7 +324,11 @@ def main():
     # end-to-end through the public API from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
-        host_blocks = [blocks[b].cpu().pin_memory() for b in range(N_BLOCKS)]
+        # pinned buffers filled straight from the device (no pageable intermediate copies)
+        host_blocks = [torch.empty(tuple(blocks[b].shape), dtype=torch.uint8, pin_memory=True) for b in range(N_BLOCKS)]
+        for b in range(N_BLOCKS):
+            host_blocks[b].copy_(blocks[b])
+        torch.cuda.synchronize()
         cross_h = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64).pin_memory()
         autos_h = torch.empty(xc.out_shape(corr.CORR_WHAT_AUTO), dtype=torch.int64).pin_memory()
 

@@ -127,7 +127,8 @@ class ClockSampler:
 def dist_setup(n_gpus):
     from paper_1411_3751_gb300 import replicas
 
-    return replicas.init("nccl")
+    # a replica that dies makes the others' next barrier fail within 10 minutes instead of hanging
+    return replicas.init("nccl", timeout_s=600)
 
 
 def barrier(world):

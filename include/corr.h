@@ -246,6 +246,15 @@ long long corr_samples_accumulated(const corr_ctx* ctx, int what);
 /* Zero the selected accumulators (what = CROSS, AUTO or CROSS|AUTO) on cuda_stream. */
 int corr_reset(corr_ctx* ctx, int what, void* cuda_stream);
 
+/*
+ * corr_selftest_wait - failure-detection self-test: enqueue on cuda_stream a one-thread kernel that
+ * waits, with the same bounded mbarrier wait the tensor-core kernels use, on a barrier phase that
+ * nothing completes. After limit_ms (1 .. 2000, else CORR_ERR_ARG) the wait gives up and records
+ * the timeout (code 90) in the context, exactly as a stalled pipeline would; the next corr_sync
+ * returns CORR_ERR_TIMEOUT and clears it, and the context stays usable. No fault, trap or hang.
+ */
+int corr_selftest_wait(corr_ctx* ctx, int limit_ms, void* cuda_stream);
+
 /* Synchronize cuda_stream; return CORR_ERR_TIMEOUT if a device-side wait gave up (flag is cleared),
  * CORR_ERR_CUDA on an asynchronous CUDA error, else CORR_OK. */
 int corr_sync(corr_ctx* ctx, void* cuda_stream);

@@ -45,6 +45,7 @@ SIGNATURES = [
     ("corr_samples_accumulated", _c_ll, [_c_vp, _c_int]),
     ("corr_reset", _c_int, [_c_vp, _c_int, _c_vp]),
     ("corr_sync", _c_int, [_c_vp, _c_vp]),
+    ("corr_selftest_wait", _c_int, [_c_vp, _c_int, _c_vp]),
     ("corr_footprint_bytes", _c_sz, [_c_int, _c_int, _c_int, _c_int, _c_int]),
     ("corr_n_baselines", _c_ll, [_c_int, _c_int]),
     ("corr_profile_enable", _c_int, [_c_vp, _c_int]),
@@ -236,6 +237,10 @@ def corr_reset(ctx: int, what: int, stream: int) -> int:
 
 def corr_sync(ctx: int, stream: int) -> int:
     return _check(_lib.corr_sync(ctx, stream), "corr_sync")
+
+
+def corr_selftest_wait(ctx: int, limit_ms: int, stream: int) -> int:
+    return _check(_lib.corr_selftest_wait(ctx, limit_ms, stream), "corr_selftest_wait")
 
 
 def corr_footprint_bytes(n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int, path: int) -> int:

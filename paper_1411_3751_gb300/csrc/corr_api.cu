@@ -536,6 +536,14 @@ int corr_set_tile_plan(corr_ctx* c, int plan) {
 
 int corr_get_tile_plan(const corr_ctx* c) { return c ? c->tile_plan : CORR_ERR_ARG; }
 
+int corr_selftest_wait(corr_ctx* c, int limit_ms, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_selftest_wait: NULL context");
+  if (limit_ms < 1 || limit_ms > 2000) return fail(CORR_ERR_ARG, "corr_selftest_wait: limit_ms must be in [1, 2000]");
+  const cudaError_t e = launch_wait_selftest(c->d_err, limit_ms, 90, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "corr_selftest_wait: launch");
+  return CORR_OK;
+}
+
 int corr_set_flush_period(corr_ctx* c, int n) {
   if (!c) return fail(CORR_ERR_ARG, "corr_set_flush_period: NULL context");
   if (n < 0 || n > kF8MaxFlush) return fail(CORR_ERR_ARG, "corr_set_flush_period: must be in [0, 65536]");

@@ -133,6 +133,10 @@ std::vector<F8Tile> f8_tile_plan(int N, int R, int plan);
 
 size_t f8_smem_bytes();
 
+// One-thread kernel whose bounded wait on a never-completed barrier gives up after limit_ms and
+// records `code` in d_err (failure-detection self-test).
+cudaError_t launch_wait_selftest(int* d_err, int limit_ms, int code, cudaStream_t st);
+
 // Dump elements [k_base, k_base + n_elems) of an accumulator, corrected with g (cross dumps: k_base
 // and n_elems even, i.e. whole (re, im) cells).
 // Selective dump of the cells among stations st[0..n_st) for channels [f0, f0 + nf) (output indexed from

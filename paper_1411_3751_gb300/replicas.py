@@ -23,19 +23,25 @@ def channel_shards(n_chans: int, world: int):
     return out
 
 
-def init(backend: str = "nccl"):
-    """(world, rank, local_rank) from the torchrun environment; joins the process group if world > 1."""
+def init(backend: str = "nccl", timeout_s: float | None = None):
+    """(world, rank, local_rank) from the torchrun environment; joins the process group if world > 1.
+
+    timeout_s bounds every collective: a rank that died or never reaches the next barrier makes the
+    others' barrier raise after at most that long instead of waiting indefinitely."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import datetime
+
         import torch
         import torch.distributed as dist
 
         if backend == "nccl":
             torch.cuda.set_device(local)
         if not dist.is_initialized():
-            dist.init_process_group(backend)
+            kw = {} if timeout_s is None else {"timeout": datetime.timedelta(seconds=timeout_s)}
+            dist.init_process_group(backend, **kw)
     return world, rank, local
 
 

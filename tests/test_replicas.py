@@ -2,6 +2,7 @@
 Each rank correlates its own contiguous channel range with no data-path collective; the shards,
 gathered here only for the check, reassemble into the single-process result."""
 import os
+import time
 import socket
 
 import numpy as np
@@ -69,3 +70,41 @@ def test_two_ranks_gloo_shards_and_timing():
     got_a = np.concatenate([s[3] for s in shards])
     assert [s[:2] for s in shards] == [(0, 6), (6, 11)]
     assert np.array_equal(got_c, want_c) and np.array_equal(got_a, want_a)
+
+
+def _dying_worker(r, w, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(r), WORLD_SIZE=str(w),
+                      LOCAL_RANK=str(r))
+    from paper_1411_3751_gb300 import replicas
+
+    replicas.init("gloo", timeout_s=10)
+    if r == 1:
+        os._exit(3)  # leaves between steps: no collective of its own in flight
+    t0 = time.monotonic()
+    try:
+        replicas.barrier(w)
+        q.put(("not detected", time.monotonic() - t0))
+    except Exception as e:  # the backend's error for a lost peer or a timed-out collective
+        q.put(("detected", time.monotonic() - t0))
+
+
+def test_a_dead_replica_is_detected_at_the_next_barrier():
+    """Two gloo ranks on CPU; rank 1 exits after joining. Rank 0's next barrier must raise (lost peer
+    or the 10 s collective timeout) instead of waiting forever."""
+    import multiprocessing as mpl
+
+    ctx = mpl.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        status, waited = q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+    assert status == "detected" and waited < 60, (status, waited)
+    assert procs[1].exitcode == 3

@@ -24,8 +24,8 @@ def main(argv=None):
     ap.add_argument("--path", default="fp8tc")
     ap.add_argument("--seed", type=int, default=0x14113751 + 2)
     ap.add_argument("--batch", action="store_true",
-                    help="accumulate the block --blocks times in one corr_accumulate_batch call (the X-engine "
-                         "launches then build the next block's operand in their background warps)")
+                    help="accumulate the block --blocks times in one corr_accumulate_batch call (the blocks "
+                         "then share tensor-core launches, as in the benchmark)")
     ap.add_argument("--pfb", action="store_true",
                     help="profile the PFB instead: --n inputs x --t spectra, 4 taps")
     ap.add_argument("--requant", action="store_true",

@@ -119,6 +119,18 @@ int corr_set_tile_plan(corr_ctx* ctx, int plan);
 int corr_get_tile_plan(const corr_ctx* ctx);
 
 /*
+ * corr_tile_plan - the work items of one channel under `plan` for n_inputs inputs (host only, no
+ * device call): returns the number of tiles and writes up to max_tiles of them to tiles_out as
+ * int[4] (c0, a0, nb, extra). A tile covers c-inputs c0 .. c0 + 63 against a-inputs a0 .. a0 + nb / 2
+ * - 1 (nb operand rows, two per input). For plan 2, extra = nb1 | (hi << 16) describes its second half:
+ * c-inputs c0 + 64 .. c0 + 127 against nb1 / 2 a-inputs from a0 + 64 hi; otherwise extra = 0.
+ * Together the tiles cover every pair a >= c of the triangle exactly once (inputs >= n_inputs are
+ * padding). CORR_ERR_ARG for n_inputs outside 1 .. 2^20, plan outside 0 .. 2, or max_tiles > 0 with
+ * a NULL buffer.
+ */
+int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
+
+/*
  * corr_set_flush_period - maximum number of samples accumulated in on-chip FP32/int32 partial sums
  * before they are added to the int64 accumulators (the paper integrates 8000-spectrum groups and
  * then sums 27 of them, Sec. 2.5; the flush cadence is this library's choice). 0 restores the

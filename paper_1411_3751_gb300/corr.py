@@ -31,6 +31,7 @@ SIGNATURES = [
     ("corr_get_path", _c_int, [_c_vp]),
     ("corr_set_tile_plan", _c_int, [_c_vp, _c_int]),
     ("corr_get_tile_plan", _c_int, [_c_vp]),
+    ("corr_tile_plan", _c_int, [_c_int, _c_int, _c_vp, _c_int]),
     ("corr_set_flush_period", _c_int, [_c_vp, _c_int]),
     ("corr_accumulate", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_accumulate_batch", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_vp]),
@@ -114,6 +115,14 @@ def corr_set_tile_plan(ctx: int, plan: int) -> int:
 
 def corr_get_tile_plan(ctx: int) -> int:
     return _check(_lib.corr_get_tile_plan(ctx), "corr_get_tile_plan")
+
+
+def corr_tile_plan(n_inputs: int, plan: int):
+    """Work items of one channel as a list of (c0, a0, nb, extra) (host only)."""
+    n = _check(_lib.corr_tile_plan(n_inputs, plan, None, 0), "corr_tile_plan")
+    buf = (ctypes.c_int * (4 * max(n, 1)))()
+    _check(_lib.corr_tile_plan(n_inputs, plan, buf, n), "corr_tile_plan")
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
 
 
 def corr_set_flush_period(ctx: int, n_samples: int) -> int:

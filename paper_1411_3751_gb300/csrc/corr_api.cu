@@ -536,6 +536,22 @@ int corr_set_tile_plan(corr_ctx* c, int plan) {
 
 int corr_get_tile_plan(const corr_ctx* c) { return c ? c->tile_plan : CORR_ERR_ARG; }
 
+int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles) {
+  if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 2 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))
+    return fail(CORR_ERR_ARG, "corr_tile_plan: need 1 <= n_inputs <= 2^20, plan 0..2, a buffer for max_tiles > 0");
+  const int R = (int)round_up(2LL * n_inputs, kF8RowAlign);
+  const std::vector<F8Tile> t = f8_tile_plan(n_inputs, R, plan);
+  if (t.size() > (size_t)0x7fffffff) return fail(CORR_ERR_ARG, "corr_tile_plan: too many tiles");
+  const int n = (int)t.size() < max_tiles ? (int)t.size() : max_tiles;
+  for (int i = 0; i < n; ++i) {
+    tiles_out[4 * i] = t[i].c0;
+    tiles_out[4 * i + 1] = t[i].a0;
+    tiles_out[4 * i + 2] = t[i].nb;
+    tiles_out[4 * i + 3] = t[i].pad;
+  }
+  return (int)t.size();
+}
+
 int corr_selftest_wait(corr_ctx* c, int limit_ms, void* stream) {
   if (!c) return fail(CORR_ERR_ARG, "corr_selftest_wait: NULL context");
   if (limit_ms < 1 || limit_ms > 2000) return fail(CORR_ERR_ARG, "corr_selftest_wait: limit_ms must be in [1, 2000]");

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,3 +89,34 @@ def test_pfb_coeffs_match_the_oracle(lib):
         np.testing.assert_array_equal(lib.corr_pfb_coeffs(n_fft, n_taps), oracle.pfb_coeffs(n_fft, n_taps))
     with pytest.raises(lib.CorrError):
         lib.corr_pfb_coeffs(100, 4)
+
+
+@pytest.mark.parametrize("plan", [0, 1, 2])
+def test_tile_plans_cover_the_triangle_exactly_once(plan):
+    """Host logic of the tensor path's work decomposition: for every input count, the tiles of a
+    channel (both halves of a plan-2 pair) cover each pair a >= c of real inputs exactly once, stay
+    within the padded operand rows, and use the MMA widths 128 and 256 only."""
+    from paper_1411_3751_gb300 import corr
+
+    for N in list(range(1, 200)) + [255, 256, 257, 383, 384, 511, 512, 513, 640, 1000, 1024]:
+        R = -(-2 * N // 128) * 128
+        seen = np.zeros((N, N), dtype=np.int32)
+        for c0, a0, nb, extra in corr.corr_tile_plan(N, plan):
+            halves = [(c0, a0, nb)]
+            if plan == 2 and extra & 0xFFFF:
+                halves.append((c0 + 64, a0 + 64 * (extra >> 16), extra & 0xFFFF))
+            else:
+                assert extra == 0 or plan == 2
+            for cc, aa, w in halves:
+                assert w in (128, 256) and cc % 64 == 0 and aa % 64 == 0
+                assert 2 * aa + w <= R and 2 * cc + 128 <= R, (N, plan, cc, aa, w)
+                c = np.arange(cc, min(cc + 64, N))[:, None]
+                a = np.arange(aa, min(aa + w // 2, N))[None, :]
+                m = (a >= c)
+                seen[np.broadcast_to(c, m.shape)[m], np.broadcast_to(a, m.shape)[m]] += 1
+        tri = np.triu(np.ones((N, N), dtype=np.int32))  # seen[c, a] for a >= c
+        assert np.array_equal(seen, tri), (N, plan)
+    with pytest.raises(corr.CorrError):
+        corr.corr_tile_plan(0, plan)
+    with pytest.raises(corr.CorrError):
+        corr.corr_tile_plan(8, 3)

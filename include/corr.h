@@ -278,6 +278,12 @@ size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int
 /* Number of station pairs B_s = S (S + 1) / 2 for n_inputs / n_pol stations (0 if invalid). */
 long long corr_n_baselines(int n_inputs, int n_pol);
 
+/* Blocks that corr_accumulate_batch multiplies per tensor-core launch for this shape (host only; 0 if
+ * invalid): as many as keep the operand rows of the channels in flight (152 CTAs / tiles per channel)
+ * within 256 MiB of L2, at most 65536 samples per launch (the exactness bound of the FP32 partial
+ * sums) and an 8 GiB operand buffer, at least one. 4 for 512 inputs x 8192-sample blocks. */
+int corr_batch_blocks(int n_inputs, int n_chans, int n_time_per_block, int n_pol);
+
 /* Enable (on != 0) or disable per-kernel timing: when enabled, every kernel the context launches is
  * bracketed by CUDA events recorded on the launching stream. Off by default. */
 int corr_profile_enable(corr_ctx* ctx, int on);

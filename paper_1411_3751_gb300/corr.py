@@ -49,6 +49,7 @@ SIGNATURES = [
     ("corr_selftest_wait", _c_int, [_c_vp, _c_int, _c_vp]),
     ("corr_footprint_bytes", _c_sz, [_c_int, _c_int, _c_int, _c_int, _c_int]),
     ("corr_n_baselines", _c_ll, [_c_int, _c_int]),
+    ("corr_batch_blocks", _c_int, [_c_int, _c_int, _c_int, _c_int]),
     ("corr_profile_enable", _c_int, [_c_vp, _c_int]),
     ("corr_profile_read", _c_int, [_c_vp, _c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     ("corr_group_create", _c_vp, [_c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _c_int, _c_int]),
@@ -258,6 +259,11 @@ def corr_footprint_bytes(n_inputs: int, n_chans: int, n_time_per_block: int, n_p
 
 def corr_n_baselines(n_inputs: int, n_pol: int) -> int:
     return int(_lib.corr_n_baselines(n_inputs, n_pol))
+
+
+def corr_batch_blocks(n_inputs: int, n_chans: int, n_time_per_block: int, n_pol: int) -> int:
+    """Blocks per tensor-core launch of corr_accumulate_batch for this shape (0 if invalid)."""
+    return int(_lib.corr_batch_blocks(n_inputs, n_chans, n_time_per_block, n_pol))
 
 
 def corr_profile_enable(ctx: int, on: int) -> int:

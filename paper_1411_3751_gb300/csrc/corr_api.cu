@@ -420,6 +420,11 @@ long long corr_n_baselines(int n_inputs, int n_pol) {
   return s * (s + 1) / 2;
 }
 
+int corr_batch_blocks(int n_inputs, int n_chans, int n_time_per_block, int n_pol) {
+  const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
+  return L.ok ? L.K_batch : 0;
+}
+
 size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int n_pol, int path) {
   const Layout L = make_layout(n_inputs, n_chans, n_time_per_block, n_pol);
   if (!L.ok || !valid_path(path)) return 0;

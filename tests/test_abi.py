@@ -120,3 +120,24 @@ def test_tile_plans_cover_the_triangle_exactly_once(plan):
         corr.corr_tile_plan(0, plan)
     with pytest.raises(corr.CorrError):
         corr.corr_tile_plan(8, 3)
+
+
+def test_batch_launch_length_rule():
+    """Host logic of corr_accumulate_batch's launch length: the benchmark's 512-input shape shares
+    4 blocks of 8192 samples per launch, 256 inputs 2; every launch stays within 65536 samples (the
+    FP32 partial sums' exactness bound) and its operand within 8 GiB unless one block alone exceeds
+    that; at least one block; invalid shapes give 0."""
+    from paper_1411_3751_gb300 import corr
+
+    assert corr.corr_batch_blocks(512, 128, 8192, 2) == 4
+    assert corr.corr_batch_blocks(256, 128, 8192, 2) == 2
+    assert corr.corr_batch_blocks(0, 1, 1, 1) == 0 and corr.corr_batch_blocks(3, 1, 1, 2) == 0
+    for N in (1, 2, 32, 64, 96, 200, 512, 1024, 2048):
+        for C in (1, 8, 128, 2400):
+            for T in (1, 240, 1000, 4096, 8192, 65536):
+                K = corr.corr_batch_blocks(N, C, T, 1 if N % 2 else 2)
+                T_pad = -(-T // 128) * 128
+                op = C * T_pad * (-(-2 * N // 32) * 32)
+                assert K >= 1, (N, C, T)
+                assert K == 1 or K * T_pad <= 65536, (N, C, T, K)
+                assert K == 1 or K * op <= 8 << 30, (N, C, T, K)

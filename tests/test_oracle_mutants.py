@@ -1,7 +1,8 @@
 """The pins must catch plausible mistakes in the oracle.
 
 * C mutants: a copy of oracle/corr_oracle.c with one deliberate error, compiled with gcc into a
-  temporary library; every mutant must fail at least two of the correlation pins.
+  temporary library; every mutant must fail at least two of the correlation pins (one for the 32-bit
+  accumulator, which only the int64 overflow pin can see).
 * numpy mutants: a copy of oracle/oracle.py with one deliberate error in the requantiser, the PFB,
   the station selection, the dump formats or the sample unpacking, executed as a separate module
   whose functions replace the oracle's; every mutant must fail at least one pin (an assertion or an
@@ -37,7 +38,26 @@ MUTANTS = {
     "transposed triangle index": (
         "const int64_t b = (int64_t)a * (a + 1) / 2 + c;",
         "const int64_t b = (int64_t)c * (c + 1) / 2 + a;"),
+    "last sample dropped from the cross sums": (
+        "for (int t = 0; t < T; ++t) {\n              /* x_i * conj(x_j)",
+        "for (int t = 0; t < T - 1; ++t) {\n              /* x_i * conj(x_j)"),
+    "32-bit cross accumulators": (
+        "int64_t acc_re = 0, acc_im = 0;",
+        "int32_t acc_re = 0, acc_im = 0;"),
+    "Im x Im dropped from the autos": (
+        "acc += (int64_t)xr[t] * xr[t] + (int64_t)xi[t] * xi[t];",
+        "acc += (int64_t)xr[t] * xr[t];"),
+    "every channel read from channel 0": (
+        "const uint8_t* row = jb->in + ((size_t)t * C + f) * N;",
+        "const uint8_t* row = jb->in + ((size_t)t * C + 0) * N;"),
+    "c-side input takes the a-side polarisation": (
+        "const int i = a * np + p, j = c * np + q;",
+        "const int i = a * np + p, j = c * np + p;"),
 }
+
+# pins each mutant must fail at least (default 2); only the int64 overflow pin can see a 32-bit
+# accumulator, since every other pin stays far below 2^31
+MIN_CAUGHT = {"32-bit cross accumulators": 1}
 
 PIN_CALLS = [
     ("brute force n_pol=1", lambda: pins.test_brute_force_every_cell(1, (7, 3, 4))),
@@ -50,6 +70,7 @@ PIN_CALLS = [
     ("invariants", pins.test_invariants_random),
     ("permutation", pins.test_permutation_of_inputs),
     ("golden fixtures", pins.test_golden_fixtures),
+    ("int64 overflow", pins.test_int64_overflow_pin),
 ]
 
 
@@ -83,7 +104,7 @@ def test_pins_catch_the_mutant(tmp_path, monkeypatch, name):
             call()
         except AssertionError:
             caught.append(label)
-    assert len(caught) >= 2, "mutant '%s' caught only by %s" % (name, caught)
+    assert len(caught) >= MIN_CAUGHT.get(name, 2), "mutant '%s' caught only by %s" % (name, caught)
 
 
 NP_MUTANTS = {

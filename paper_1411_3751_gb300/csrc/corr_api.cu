@@ -11,41 +11,32 @@
 #include <tuple>
 #include <vector>
 
+#include "corr_ctx.cuh"
 #include "corr_internal.cuh"
 
 #include <cmath>
 
 using namespace corr;
+using namespace corr::host;
 
-namespace {
+namespace corr {
+namespace host {
 
 thread_local std::string g_err;
+
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
-
 int cuda_fail(cudaError_t e, const char* what) {
   return fail(CORR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+
 constexpr size_t kStageBytes = 64ull << 20;     // host-dump staging buffer, x2
 constexpr size_t kMaxInStage = 512ull << 20;    // host-input staging buffer (per buffer), x2
 
-struct Layout {
-  Shape s;
-  long long cross_elems;  // int64 elements
-  long long autos_elems;
-  int R;                  // FP8 operand rows per sample as the tiles see them: round_up(2N, 128)
-  int R_buf;              // operand rows stored per sample: round_up(2N, 32); the TMA fills rows
-                          // R_buf .. R - 1 of a tile with zeros (out of the tensor map's extent)
-  int T_pad;              // FP8 operand samples per channel and block
-  size_t op_bytes;        // one block's operand
-  int K_batch;            // blocks per operand buffer (one tensor-core launch in a batch)
-  size_t op_buf_bytes;    // K_batch blocks' operand
-  bool ok;
-};
 
 bool mul_ok(unsigned long long a, unsigned long long b, unsigned long long* out) {
   if (a != 0 && b > ~0ull / a) return false;
@@ -117,7 +108,8 @@ std::vector<int2> fp32_tiles(int N) {
   return t;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace corr
 
 namespace corr {
 void set_last_error(const std::string& msg) { g_err = msg; }
@@ -136,55 +128,10 @@ cudaError_t set_smem_limit(const void* func, int bytes) {
 }
 }  // namespace corr
 
-// Opt-in per-kernel timing: CUDA events recorded on the launching stream around each launch.
-struct KernelTimer {
-  std::vector<cudaEvent_t> ev;  // pairs (start, stop)
-  size_t used = 0;
-  long long launches = 0;
-  double ms = 0.0;
-};
 
-struct corr_ctx {
-  Layout L;
-  bool profiling;
-  KernelTimer timers[CORR_KERNEL_COUNT];
-  int path;
-  int flush_len;  // 0 = path default
-  int device;
-  int num_sms;
-  long long* d_cross;
-  long long* d_autos;
-  long long* d_soff;       // [C][N][2] offset sums of the tensor paths (cross cadence)
-  long long* d_soff_auto;  // same, total-power cadence
-  long long n_off;         // samples accumulated through a tensor path since the cross reset
-  long long n_off_auto;    // same, since the autos reset
-  int* d_err;
-  uint8_t* d_op;          // operand scratch of the two-pass tensor path (K_batch blocks)
-  CUtensorMap tmap;
-  int2* d_tiles32;
-  int n_tiles32;
-  F8Tile* d_tiles8;        // tile list (current plan), used by the fused path
-  int n_tiles8;
-  WorkItem* d_items;       // channel-major work list of the two-pass tensor path
-  long long n_items;
-  int tile_plan;
-  void* d_stage[2];      // host dumps
-  void* d_in_stage[2];   // host inputs
-  size_t in_stage;
-  cudaStream_t copy_stream;
-  cudaEvent_t ev_copied[2], ev_free[2];
-  bool free_recorded[2];
-  int next_in;
-  long long n_cross;
-  long long n_auto;
-  // selective dumps: station list scratch and the per-cell sample counts at the last selective reset
-  int* d_sel;
-  int sel_cap;
-  long long* d_cross_base;  // [B_s], allocated at the first selective cross reset
-  long long* d_auto_base;   // [N], allocated at the first selective autos reset
-};
 
-namespace {
+namespace corr {
+namespace host {
 
 int resolved_path(const corr_ctx* c) { return c->path == CORR_PATH_AUTO ? CORR_PATH_FP8TC : c->path; }
 
@@ -193,6 +140,7 @@ bool valid_path(int path) {
          path == CORR_PATH_FP8TC_FUSED;
 }
 
+
 int flush_for(const corr_ctx* c, int path) {
   if (c->flush_len > 0) {
     const int g = path == CORR_PATH_FP32 ? kF32Kt : kF8Kt;
@@ -200,6 +148,7 @@ int flush_for(const corr_ctx* c, int path) {
   }
   return path == CORR_PATH_FP32 ? kDefaultFlushF32 : kDefaultFlushF8;
 }
+
 
 // Sum and recycle recorded event pairs (synchronizes on the last recorded stop event).
 void drain_timer(KernelTimer& t) {
@@ -210,6 +159,7 @@ void drain_timer(KernelTimer& t) {
   }
   t.used = 0;
 }
+
 
 bool timer_begin(corr_ctx* c, int k, cudaStream_t st) {
   if (!c->profiling) return false;
@@ -223,7 +173,6 @@ bool timer_begin(corr_ctx* c, int k, cudaStream_t st) {
   cudaEventRecord(t.ev[2 * t.used], st);
   return true;
 }
-
 void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun) {
   if (!begun) return;
   KernelTimer& t = c->timers[k];
@@ -231,6 +180,7 @@ void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun) {
   ++t.used;
   ++t.launches;
 }
+
 
 void free_ctx(corr_ctx* c) {
   if (!c) return;
@@ -260,10 +210,10 @@ void free_ctx(corr_ctx* c) {
   delete c;
 }
 
-int set_tile_plan(corr_ctx* c, int plan);
 XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush);
 
 // Accumulate T_blk samples from a device buffer laid out [T_blk][C][N].
+
 int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t st) {
   const int path = resolved_path(c);
   const int flush = flush_for(c, path);
@@ -303,8 +253,10 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
   return CORR_OK;
 }
 
+
 // Tile plan of the tensor paths: the tile list (fused path) and the channel-major work list
 // (two-pass path) for plan 0, 1 or 2 (see f8_tile_plan).
+
 int set_tile_plan(corr_ctx* c, int plan) {
   // the fused path has no wide mode: it keeps plan 0 under plan 2
   const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan == 2 ? 0 : plan);
@@ -337,6 +289,7 @@ int set_tile_plan(corr_ctx* c, int plan) {
   c->tile_plan = plan;
   return CORR_OK;
 }
+
 
 XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush) {
   XengArgs a;
@@ -406,7 +359,8 @@ int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cu
   return CORR_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace corr
 
 extern "C" {
 
@@ -904,293 +858,6 @@ int corr_destroy(corr_ctx* c) {
   free_ctx(c);
   if (e != cudaSuccess) return cuda_fail(e, "corr_destroy: synchronize");
   return CORR_OK;
-}
-
-}  // extern "C"
-
-// =============================================================================================
-// Groups of sub-arrays (different N and C, one block length): one persistent tensor-core launch
-// covers the work items of every sub-array; per-array tile plans come from a small autotuner.
-// =============================================================================================
-
-struct corr_group {
-  int n;
-  corr_ctx* ctx[kMaxGroupArrays];
-  WorkItem* d_items;
-  long long n_items;
-  cudaGraphExec_t graph;
-  int T;
-};
-
-namespace {
-
-// autotuner cache: (N, C, T, n_pol, SMs) -> tile plan; optionally mirrored in the file named by the
-// CORR_AUTOTUNE_CACHE environment variable (lines "N C T n_pol SMs plan")
-std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune;
-bool g_tune_loaded = false;
-
-void tune_load() {
-  if (g_tune_loaded) return;
-  g_tune_loaded = true;
-  const char* path = std::getenv("CORR_AUTOTUNE_CACHE");
-  if (!path) return;
-  FILE* fh = std::fopen(path, "r");
-  if (!fh) return;
-  int a, b, c, d, e, p;
-  while (std::fscanf(fh, "%d %d %d %d %d %d", &a, &b, &c, &d, &e, &p) == 6) g_tune[std::make_tuple(a, b, c, d, e)] = p;
-  std::fclose(fh);
-}
-
-void tune_store(const std::tuple<int, int, int, int, int>& k, int plan) {
-  g_tune[k] = plan;
-  const char* path = std::getenv("CORR_AUTOTUNE_CACHE");
-  if (!path) return;
-  FILE* fh = std::fopen(path, "a");
-  if (!fh) return;
-  std::fprintf(fh, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-               std::get<4>(k), plan);
-  std::fclose(fh);
-}
-
-// Group work list: arrays in order of decreasing N (largest tiles first), each channel-major.
-int group_build_items(corr_group* g) {
-  std::vector<int> order(g->n);
-  for (int i = 0; i < g->n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return g->ctx[x]->L.s.N > g->ctx[y]->L.s.N; });
-  std::vector<WorkItem> items;
-  for (int i : order) {
-    corr_ctx* c = g->ctx[i];
-    // group launches run the default mode: a member on plan 2 joins with plan 0
-    const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan == 2 ? 0 : c->tile_plan);
-    for (int f = 0; f < c->L.s.C; ++f)
-      for (const F8Tile& t : t8) items.push_back(WorkItem{i, f, t.c0, t.a0, t.nb, 0});
-  }
-  WorkItem* d = nullptr;
-  if (cudaMalloc(&d, items.size() * sizeof(WorkItem)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(CORR_ERR_OOM, "group work list allocation failed");
-  }
-  cudaError_t e = cudaMemcpy(d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(d);
-    return cuda_fail(e, "group work list upload");
-  }
-  cudaFree(g->d_items);
-  g->d_items = d;
-  g->n_items = (long long)items.size();
-  return CORR_OK;
-}
-
-// One grouped accumulate: operand build per array, then one persistent launch over all arrays.
-int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
-  corr_ctx* c0 = g->ctx[0];
-  const int T_pad = c0->L.T_pad;
-  XengArgs a;
-  std::memset(&a, 0, sizeof(a));
-  for (int i = 0; i < g->n; ++i)
-    if (!g->ctx[i]->d_op)
-      return fail(CORR_ERR_STATE, "group member " + std::to_string(i) +
-                                      " has no operand scratch (its path was set to FP32 or int8; set a tensor path)");
-  for (int i = 0; i < g->n; ++i) {
-    corr_ctx* c = g->ctx[i];
-    bool tb = timer_begin(c0, CORR_KERNEL_UNPACK, st);
-    cudaError_t e = launch_f8_prep(c->L.s, in[i], c->L.s.T, T_pad, c->L.T_pad * c->L.K_batch, 0, c->L.R_buf, c->d_op,
-                                   c->d_soff, c->d_soff_auto, st);
-    timer_end(c0, CORR_KERNEL_UNPACK, st, tb);
-    if (e != cudaSuccess) return cuda_fail(e, "group operand build");
-    a.a[i].tmap = c->tmap;
-    a.a[i].cross = c->d_cross;
-    a.a[i].autos = c->d_autos;
-    a.a[i].Bs = c->L.s.Bs;
-    a.a[i].N = c->L.s.N;
-    a.a[i].npol = c->L.s.npol;
-  }
-  a.items = g->d_items;
-  a.n_items = g->n_items;
-  a.T_run = T_pad;
-  a.flush_len = flush_for(c0, CORR_PATH_FP8TC);
-  a.err = c0->d_err;
-  const bool tb = timer_begin(c0, CORR_KERNEL_XENG, st);
-  cudaError_t e = launch_f8_xeng(a, c0->num_sms, st);
-  timer_end(c0, CORR_KERNEL_XENG, st, tb);
-  if (e != cudaSuccess) return cuda_fail(e, "group x-engine launch");
-  return CORR_OK;
-}
-
-void group_count(corr_group* g) {
-  for (int i = 0; i < g->n; ++i) {
-    corr_ctx* c = g->ctx[i];
-    c->n_cross += c->L.s.T;
-    c->n_auto += c->L.s.T;
-    c->n_off += c->L.s.T;
-    c->n_off_auto += c->L.s.T;
-  }
-}
-
-}  // namespace
-
-extern "C" {
-
-corr_group* corr_group_create(int n_arrays, const int* n_inputs, const int* n_chans, int n_time_per_block, int n_pol) {
-  if (n_arrays < 1 || n_arrays > kMaxGroupArrays || !n_inputs || !n_chans) {
-    fail(CORR_ERR_ARG, "corr_group_create: need 1.." + std::to_string(kMaxGroupArrays) + " sub-arrays");
-    return nullptr;
-  }
-  corr_group* g = new (std::nothrow) corr_group{};
-  if (!g) {
-    fail(CORR_ERR_OOM, "corr_group_create: host allocation");
-    return nullptr;
-  }
-  g->n = n_arrays;
-  g->T = n_time_per_block;
-  for (int i = 0; i < n_arrays; ++i) {
-    g->ctx[i] = corr_create(n_inputs[i], n_chans[i], n_time_per_block, n_pol);
-    if (!g->ctx[i]) {
-      const std::string msg = g_err;
-      corr_group_destroy(g);
-      fail(CORR_ERR_ARG, "corr_group_create: sub-array " + std::to_string(i) + ": " + msg);
-      return nullptr;
-    }
-  }
-  if (group_build_items(g) != CORR_OK) {
-    const std::string msg = g_err;
-    corr_group_destroy(g);
-    fail(CORR_ERR_OOM, "corr_group_create: " + msg);
-    return nullptr;
-  }
-  return g;
-}
-
-corr_ctx* corr_group_member(corr_group* g, int i) {
-  if (!g || i < 0 || i >= g->n) {
-    fail(CORR_ERR_ARG, "corr_group_member: bad index");
-    return nullptr;
-  }
-  return g->ctx[i];
-}
-
-int corr_group_accumulate(corr_group* g, const void* const* d_samples, int mode, void* stream) {
-  if (!g || !d_samples) return fail(CORR_ERR_ARG, "corr_group_accumulate: NULL argument");
-  for (int i = 0; i < g->n; ++i)
-    if (!d_samples[i]) return fail(CORR_ERR_ARG, "corr_group_accumulate: NULL block " + std::to_string(i));
-  cudaStream_t st = (cudaStream_t)stream;
-  const uint8_t* const* in = reinterpret_cast<const uint8_t* const*>(d_samples);
-  if (mode == 1) {
-    for (int i = 0; i < g->n; ++i) {
-      const int rc = corr_accumulate(g->ctx[i], d_samples[i], stream);
-      if (rc != CORR_OK) return rc;
-    }
-    return CORR_OK;
-  }
-  if (mode != 0) return fail(CORR_ERR_ARG, "corr_group_accumulate: mode must be 0 (grouped) or 1 (separate)");
-  const int rc = group_enqueue(g, in, st);
-  if (rc != CORR_OK) return rc;
-  group_count(g);
-  return CORR_OK;
-}
-
-int corr_group_autotune(corr_group* g, const void* const* d_samples, int* plans_out, void* stream) {
-  if (!g || !d_samples) return fail(CORR_ERR_ARG, "corr_group_autotune: NULL argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  tune_load();
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return cuda_fail(cudaGetLastError(), "corr_group_autotune: events");
-  int rc = CORR_OK;
-  for (int i = 0; i < g->n && rc == CORR_OK; ++i) {
-    corr_ctx* c = g->ctx[i];
-    const auto key = std::make_tuple(c->L.s.N, c->L.s.C, c->L.s.T, c->L.s.npol, c->num_sms);
-    auto it = g_tune.find(key);
-    int best = 0;
-    if (it != g_tune.end()) {
-      best = it->second;
-    } else {
-      float best_ms = 1e30f;
-      for (int plan = 0; plan < 2 && rc == CORR_OK; ++plan) {
-        rc = set_tile_plan(c, plan);
-        if (rc != CORR_OK) break;
-        // one warm-up block, then three timed blocks through the tensor path of this array alone
-        for (int rep = 0; rep < 4 && rc == CORR_OK; ++rep) {
-          if (rep == 1) cudaEventRecord(e0, st);
-          rc = accumulate_device(c, static_cast<const uint8_t*>(d_samples[i]), c->L.s.T, st);
-        }
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "corr_group_autotune");
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = plan;
-        }
-      }
-      if (rc == CORR_OK) tune_store(key, best);
-    }
-    if (rc == CORR_OK) rc = set_tile_plan(c, best);
-    if (rc == CORR_OK) rc = corr_reset(c, CORR_WHAT_CROSS | CORR_WHAT_AUTO, stream);
-    if (plans_out) plans_out[i] = best;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (rc != CORR_OK) return rc;
-  // a captured graph refers to the old work list: drop it (corr_group_capture records a new one)
-  if (g->graph) {
-    cudaGraphExecDestroy(g->graph);
-    g->graph = nullptr;
-  }
-  return group_build_items(g);
-}
-
-int corr_group_capture(corr_group* g, const void* const* d_samples, void* stream) {
-  if (!g || !d_samples) return fail(CORR_ERR_ARG, "corr_group_capture: NULL argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!st) return fail(CORR_ERR_ARG, "corr_group_capture: needs a non-default stream");
-  bool prof[kMaxGroupArrays];
-  for (int i = 0; i < g->n; ++i) {
-    prof[i] = g->ctx[i]->profiling;
-    g->ctx[i]->profiling = false;  // no timing events inside the graph
-  }
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-  int rc = CORR_OK;
-  if (e == cudaSuccess) {
-    rc = group_enqueue(g, reinterpret_cast<const uint8_t* const*>(d_samples), st);
-    e = cudaStreamEndCapture(st, &graph);
-  }
-  for (int i = 0; i < g->n; ++i) g->ctx[i]->profiling = prof[i];
-  if (rc != CORR_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "corr_group_capture: capture");
-  cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "corr_group_capture: instantiate");
-  if (g->graph) cudaGraphExecDestroy(g->graph);
-  g->graph = exec;
-  return CORR_OK;
-}
-
-int corr_group_launch(corr_group* g, void* stream) {
-  if (!g) return fail(CORR_ERR_ARG, "corr_group_launch: NULL group");
-  if (!g->graph) return fail(CORR_ERR_STATE, "corr_group_launch: no captured graph (call corr_group_capture)");
-  cudaError_t e = cudaGraphLaunch(g->graph, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "corr_group_launch");
-  group_count(g);
-  return CORR_OK;
-}
-
-int corr_group_destroy(corr_group* g) {
-  if (!g) return CORR_OK;
-  int rc = CORR_OK;
-  if (g->graph) cudaGraphExecDestroy(g->graph);
-  cudaFree(g->d_items);
-  for (int i = 0; i < g->n; ++i)
-    if (g->ctx[i] && corr_destroy(g->ctx[i]) != CORR_OK) rc = CORR_ERR_CUDA;
-  delete g;
-  return rc;
 }
 
 }  // extern "C"

@@ -226,13 +226,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--path", default="fp8tc", choices=["fp8tc", "fp8tc_fused", "i8mma", "fp32"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="steps of the end-to-end leg (default: as many as --steps; 0 skips it)")
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--i8-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.e2e_steps < 0:
+        args.e2e_steps = args.steps
     if args.impl == "reference":
         return run_reference(args)
 

@@ -39,6 +39,17 @@ def test_reference_arm_line():
     assert line["config"]["n_inputs"] == 512 and line["config"]["n_chans"] == 128
 
 
+def test_reference_arm_other_ranks_exit_quietly():
+    """Launched as rank 1 of 2 (as torchrun would), the reference arm does no work, prints nothing
+    and exits 0; rank 0 alone prints the line."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", MASTER_ADDR="127.0.0.1", MASTER_PORT="29599")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300,
+                         env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
 @pytest.mark.gpu
 def test_native_arm_line():
     line = _run(["--steps", "2", "--warmup", "3", "--e2e-steps", "1", "--fp32-steps", "0", "--i8-steps", "0",

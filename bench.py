@@ -41,25 +41,107 @@ def useful_cmacs(N, C, T):
     return N * (N + 1) // 2 * C * T
 
 
+def source_hash(kernel_files):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in kernel_files:
+        h.update(open(os.path.join(ROOT, "paper_1411_3751_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel_files, profile_md, blocks_per_launch):
     """DRAM bytes per launch recorded by an ncu capture (profiles/), if the kernel sources still match
     and the capture covered launches of the same size."""
-    import hashlib
-
     try:
         text = open(os.path.join(ROOT, "profiles", profile_md)).read()
-        h = hashlib.sha256()
-        for f in kernel_files:
-            h.update(open(os.path.join(ROOT, "paper_1411_3751_gb300", "csrc", f), "rb").read())
         keys = ("traffic_bytes_per_launch:", "source_sha256:", "blocks_per_launch:")
         vals = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(keys))
-        if vals.get("source_sha256", "").strip() != h.hexdigest()[:16]:
+        if vals.get("source_sha256", "").strip() != source_hash(kernel_files):
             return None
         if abs(float(vals.get("blocks_per_launch", "1")) - blocks_per_launch) > 1e-9:
             return None
         return int(vals["traffic_bytes_per_launch"])
     except Exception:
         return None
+
+
+XENG_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"]
+PREP_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh"]
+
+
+def step_traffic(xeng_launches, prep_launches, blocks_per_launch):
+    """DRAM bytes of one step from the ncu captures summarised in profiles/ (per launch, source-hash
+    checked) against the algorithmic bytes of the step: the input read once, the int64 cross
+    accumulators read and written once per X-engine launch, and the dumped visibilities written once."""
+    from paper_1411_3751_gb300 import corr
+
+    acc = N_CHAN * corr.corr_n_baselines(N_IN, N_POL) * N_POL * N_POL * 2 * 8
+    inp = T_BLOCK * N_BLOCKS * N_CHAN * N_IN
+    alg = inp + xeng_launches * 2 * acc + acc
+    x = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch)
+    pr = profiled_traffic(PREP_SOURCES, "f8_prep_512in_128ch_8192.md", 1)
+    out = {"algorithmic_bytes": alg, "xeng_bytes_per_launch": x, "prep_bytes_per_launch": pr,
+           "xeng_launches": xeng_launches, "prep_launches": prep_launches}
+    if x is not None and pr is not None:
+        dump = 3 * acc  # dump kernels (not captured) at their own algorithmic bytes: read, write, reset
+        meas = x * xeng_launches + pr * prep_launches + dump
+        out.update({"measured_bytes": meas, "ratio": meas / alg})
+    return out
+
+
+def run_extras():
+    """The other workloads of the metric, shortened so the whole benchmark stays within minutes:
+    flush overhead at 512 inputs x 256 channels x 65536 samples (saturating inputs), five uneven
+    sub-arrays in one grouped graph-replayed launch vs separate launches, the streaming loop over
+    18 s of data (two 9 s cross dumps and eighteen 1 s total-power dumps per stream), and the 32- and
+    64-input arrays against the HBM copy bandwidth."""
+    import torch
+
+    from paper_1411_3751_gb300 import corr, measure_configs, synth
+
+    out = {}
+    for name, fn in (("precision", lambda: measure_configs.precision(corr, synth, torch, reps=2)),
+                     ("group", lambda: measure_configs.group(corr, synth, torch, reps=5)),
+                     ("stream", lambda: measure_configs.stream_loop(corr, synth, torch, n_blocks=1800)),
+                     ("small", lambda: measure_configs.small(corr, synth, torch, reps=3))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:  # a failing extra must not cost the headline line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    return out
+
+
+def issued_flops_per_sample(n_inputs, n_chans):
+    """MMA flops the tensor path issues per sample (tile plan 0: 128 x nb x 32 instructions), split
+    into wide (N = 256) and narrow (N = 128) instructions."""
+    from paper_1411_3751_gb300 import corr
+
+    wide = narrow = 0
+    for _c0, _a0, nb, _x in corr.corr_tile_plan(n_inputs, 0):
+        if nb > 128:
+            wide += 2 * 128 * nb * n_chans
+        else:
+            narrow += 2 * 128 * nb * n_chans
+    return wide, narrow
+
+
+def roofline_peak(peaks, clk, timed_s):
+    """FP8 tensor peak from the measured bf16 GEMM rate (x 2, the nominal fp8/bf16 ratio): the burst
+    figure when the kernel ran at the maximum SM clock with no power cap over a short timed region
+    (under a second), else the sustained figure (a seconds-long loop under the power cap)."""
+    at_max = bool(clk.get("sm_mhz") and clk.get("sm_max_mhz") and clk["sm_mhz"] >= 0.98 * clk["sm_max_mhz"])
+    capped = "sw_power_cap" in (clk.get("reasons") or [])
+    burst = at_max and not capped and timed_s < 1.0
+    key = "bf16_tflops" if burst else "bf16_tflops_sustained"
+    val = peaks.get(key, peaks.get("bf16_tflops"))
+    why = ("SM clock at its maximum, no power cap, %.2f s timed" % timed_s if burst else
+           "SM clock %s of %s MHz, power cap %s, %.2f s timed" % (clk.get("sm_mhz"), clk.get("sm_max_mhz"),
+                                                                 "active" if capped else "inactive", timed_s))
+    return 2.0 * float(val), ("burst" if burst else "sustained"), why
 
 
 def load_peaks():
@@ -231,6 +313,9 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--i8-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the flush-overhead, grouped-launch, streaming and small-array measurements")
+    ap.add_argument("--no-probe", action="store_true", help="skip the tcgen05 issue-rate probe")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -267,6 +352,14 @@ def main():
     for _ in range(args.warmup):
         step()
     xc.sync()
+    # the tcgen05 issue rate of this GPU at its current clock, just before the timed region
+    probe = None
+    if args.path.startswith("fp8tc") and not args.no_probe:
+        r256 = corr.corr_probe_mma_rate(16384, 256, stream.cuda_stream)
+        r128 = corr.corr_probe_mma_rate(16384, 128, stream.cuda_stream)
+        probe = {"tflops_n256": r256[0], "cycles_per_mma_n256": r256[1], "tflops_n128": r128[0],
+                 "cycles_per_mma_n128": r128[1], "mma_per_sm": 16384,
+                 "what": "tcgen05.mma kind::f8f6f4 M=128 K=32 back to back from unchanging shared memory, one CTA per SM"}
     # timed region
     clocks = ClockSampler(local)
     clocks.start()
@@ -302,8 +395,8 @@ def main():
     blocks_per_launch = N_BLOCKS * args.steps / max(1, xeng_n)
     flops_launch = 8.0 * useful_cmacs(N_IN, N_CHAN, T_BLOCK) * blocks_per_launch
     if args.path.startswith("fp8tc"):
-        peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-        peak_note = "%s bf16 sustained x 2 (nominal fp8/bf16 ratio)" % peak_src
+        peak, which, why = roofline_peak(peaks, clk, ms_total / 1e3)
+        peak_note = "%s bf16 %s x 2 (nominal fp8/bf16 ratio): %s" % (peak_src, which, why)
         bound = "tensor"
     elif args.path == "i8mma":
         peak = 158.0  # mma.sync m16n8k32 s8 throughput measured by a microbenchmark on this GPU
@@ -316,14 +409,25 @@ def main():
     achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
     traffic = None
     if args.path == "fp8tc":
-        traffic = profiled_traffic(["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"], "f8_xeng_512in_128ch_8192.md",
-                                   blocks_per_launch)
+        traffic = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel",
                                            "i8mma": "xeng_i8mma_kernel"}.get(args.path, "xeng_fp32_kernel"),
             "peak_source": peak_note, "launch_ms": per_launch_ms,
             "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop (%.0f blocks of 8192 samples per launch)"
                            % (flops_launch, blocks_per_launch)}
+    if args.path.startswith("fp8tc") and probe:
+        # the same kernel against the tcgen05 issue rate measured on this GPU just before the timed
+        # region: the ideal launch time of the MMAs the tile plan issues, and the useful rate's share
+        wide, narrow = issued_flops_per_sample(N_IN, N_CHAN)
+        samples = T_BLOCK * blocks_per_launch
+        ideal_ms = (wide * samples / (probe["tflops_n256"] * 1e12) + narrow * samples / (probe["tflops_n128"] * 1e12)) * 1e3
+        roof["issue_probe"] = dict(probe)
+        roof["issued_flop_per_launch"] = (wide + narrow) * samples
+        roof["frac_issue"] = ideal_ms / per_launch_ms
+        roof["frac_useful_of_issue_peak"] = achieved / probe["tflops_n256"]
+    if args.path == "fp8tc":
+        roof["step_traffic"] = step_traffic(xeng_n / args.steps, unpack_n / args.steps, blocks_per_launch)
 
     # end-to-end through the public API from pinned host buffers
     e2e = None
@@ -401,6 +505,11 @@ def main():
     fp32 = path_leg("fp32", args.fp32_steps)
     xc.sync()
     xc.close()
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        del blocks, cross_out, autos_out
+        torch.cuda.empty_cache()
+        extras = run_extras()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,6 +536,8 @@ def main():
             "fp32_path": fp32,
             "cpu_baseline": cpu,
         }
+        if extras is not None:
+            line["configs"] = extras
         print(json.dumps(line))
     from paper_1411_3751_gb300 import replicas
 

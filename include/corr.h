@@ -321,6 +321,19 @@ int corr_xengine_static(const void* d_samples, int n_inputs, int n_chans, int n_
                         long long* d_autos, void* cuda_stream);
 
 /*
+ * corr_probe_mma_rate - issue-rate probe of the tensor instruction the X-engine is built on. No
+ * counterpart in the paper: a measurement helper. One CTA per SM issues n_mma (1 .. 2^20)
+ * back-to-back tcgen05.mma kind::f8f6f4 instructions (e4m3 operands in unchanging shared-memory
+ * tiles, M = 128, N = n_cols (128 or 256), K = 32, FP32 accumulation in TMEM), once to warm up and
+ * once timed with CUDA events on cuda_stream; synchronizes. Writes (host pointers, either may be
+ * NULL) the rate in TFLOP/s, 2 * 128 * n_cols * 32 * n_mma * SMs / elapsed, and the median SM cycles
+ * per MMA (clock64). This is the ceiling a single-SM tcgen05 X-engine can reach on this device at its
+ * current clock. Allocates and frees a few bytes of device memory. CORR_ERR_ARG for other sizes,
+ * CORR_ERR_TIMEOUT if the completion wait gave up (2 s), CORR_ERR_CUDA on a CUDA error.
+ */
+int corr_probe_mma_rate(int n_mma, int n_cols, double* tflops, double* cycles_per_mma, void* cuda_stream);
+
+/*
  * Groups of sub-arrays. The paper's architecture scales by giving each GPU its own slice of the
  * problem (Sec. 2.5, Sec. 6: 109 channels per GPU, the same code from 32 to 512 inputs); a group
  * correlates several independent sub-arrays of different input and channel counts (sharing the

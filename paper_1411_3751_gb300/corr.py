@@ -60,6 +60,8 @@ SIGNATURES = [
     ("corr_group_launch", _c_int, [_c_vp, _c_vp]),
     ("corr_group_destroy", _c_int, [_c_vp]),
     ("corr_xengine_static", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),
+    ("corr_probe_mma_rate", _c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     _c_vp]),
     ("corr_destroy", _c_int, [_c_vp]),
     ("corr_last_error", _c_cp, []),
     ("corr_version", _c_cp, []),
@@ -283,6 +285,14 @@ def corr_xengine_static(d_samples: int, n_inputs: int, n_chans: int, n_time: int
     """Allocation-free tensor-path X-engine for one block (adds into d_cross / d_autos)."""
     return _check(_lib.corr_xengine_static(d_samples, n_inputs, n_chans, n_time, n_pol, d_cross, d_autos, stream),
                   "corr_xengine_static")
+
+
+def corr_probe_mma_rate(n_mma: int, n_cols: int, stream: int):
+    """Issue rate of the X-engine's tcgen05 MMA with no operand traffic: (TFLOP/s, cycles per MMA)."""
+    tf = ctypes.c_double(0.0)
+    cyc = ctypes.c_double(0.0)
+    _check(_lib.corr_probe_mma_rate(n_mma, n_cols, ctypes.byref(tf), ctypes.byref(cyc), stream), "corr_probe_mma_rate")
+    return tf.value, cyc.value
 
 
 def _ptr_array(ptrs):

@@ -239,7 +239,7 @@ cudaError_t launch_dump_select(long long* d_acc, const int* d_st, int n_st, int 
   const long long units = (long long)nf * (g.autos ? (long long)n_st * g.npol : (long long)n_st * (n_st + 1) / 2 * g.P);
   if (units == 0) return cudaSuccess;
   long long blocks = (units + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > (long long)sm_count() * 32) blocks = (long long)sm_count() * 32;
   dump_select_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, d_st, n_st, f0, nf, d_out, fmt, n_samples, reset, g);
   return cudaGetLastError();
 }
@@ -248,7 +248,7 @@ cudaError_t launch_set_base(long long* d_base, const int* d_st, int n_st, long l
                             cudaStream_t st) {
   const long long n = g.autos ? (long long)n_st * g.npol : (long long)n_st * (n_st + 1) / 2;
   long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > (long long)sm_count() * 8) blocks = (long long)sm_count() * 8;
   if (blocks == 0) return cudaSuccess;
   set_base_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_base, d_st, n_st, value, g.npol, g.autos);
   return cudaGetLastError();
@@ -259,7 +259,7 @@ cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, 
   if (n_elems == 0) return cudaSuccess;
   const long long n_units = g.autos ? n_elems : n_elems / 2;
   long long blocks = (n_units + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > (long long)sm_count() * 32) blocks = (long long)sm_count() * 32;
   if (g.autos)
     dump_autos_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_acc, k_base, n_elems, d_out, fmt, n_samples, g);
   else

@@ -71,7 +71,7 @@ Layout make_layout(int N, int C, int T, int npol) {
   // blocks per batch launch: the operand of the channels in flight within kL2Window (see there),
   // at most kF8MaxFlush samples per launch, and a buffer is capped at kMaxOperandBuffer
   const long long tiles_per_chan = (long long)f8_tile_plan(N, L.R, 0).size();
-  double in_flight = (double)kSmCount / (double)(tiles_per_chan > 0 ? tiles_per_chan : 1);
+  double in_flight = (double)sm_count() / (double)(tiles_per_chan > 0 ? tiles_per_chan : 1);
   if (in_flight < 1.0) in_flight = 1.0;
   const double t_launch = (double)kL2Window / (in_flight * (double)L.R_buf);
   long long k = (long long)(t_launch / (double)L.T_pad);
@@ -113,6 +113,26 @@ std::vector<int2> fp32_tiles(int N) {
 
 namespace corr {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return kDefaultSmCount;
+  }
+  static std::mutex m;
+  static std::map<int, int> cache;
+  std::lock_guard<std::mutex> lock(m);
+  const auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = kDefaultSmCount;
+  }
+  cache[dev] = n;
+  return n;
+}
 
 cudaError_t set_smem_limit(const void* func, int bytes) {
   static std::mutex m;

@@ -88,11 +88,15 @@ constexpr unsigned long long kMaxOperandBuffer = 8ull << 30;  // per two-pass op
 // Samples per tensor-core launch in a batch: long enough that the int64 accumulators (read and
 // written once per launch) cost little, short enough that the operand rows the CTAs working at the
 // same time share stay in L2: about kL2Window bytes of operand across the channels in flight
-// (kSmCount CTAs / tiles per channel). Measured at 512 inputs (1 KiB of operand per sample and
+// (one CTA per SM / tiles per channel). Measured at 512 inputs (1 KiB of operand per sample and
 // channel, 20 tiles per channel), per launch: 8192 samples 198, 16384 207, 32768 212, 49152 190,
 // 65536 151 Tera-CMAC/s.
 constexpr unsigned long long kL2Window = 256ull << 20;
-constexpr int kSmCount = 152;
+// SM count assumed by host-only queries when no device is present (a GB300 has 152).
+constexpr int kDefaultSmCount = 152;
+// Multiprocessor count of the current device (cached per device; thread-safe), or kDefaultSmCount
+// when no device is available.
+int sm_count();
 
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 

@@ -184,7 +184,7 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   if (e == cudaSuccess) {
     const long long n_cells = (long long)n_chans * sh.Bs * sh.P;
     long long blocks = (n_cells + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
     static_correct_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_cross, n_cells, d_autos, (long long)n_chans * n_inputs,
                                                             n_inputs, n_pol, sh.Bs, d_s, (long long)n_time);
     e = cudaGetLastError();

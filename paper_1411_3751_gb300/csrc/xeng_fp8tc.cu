@@ -374,7 +374,8 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
   // enough blocks for ~7 waves at 2 blocks per SM, so the last partial wave is a small share of the
   // launch (measured at 512 inputs: 3.4 waves 0.273 ms per 8192-sample block, 6.7 waves 0.257 ms,
   // 13.5 waves 0.257 ms, 27 waves 0.265 ms)
-  while ((units + 7) / 8 * split < 8LL * kSmCount && T_run / (split * 2) >= 256) split *= 2;
+  const long long target = 8LL * sm_count();
+  while ((units + 7) / 8 * split < target && T_run / (split * 2) >= 256) split *= 2;
   const int rows = (int)round_up((T_run + split - 1) / split, 32);
   split = (T_run + rows - 1) / rows;
   dim3 grid((unsigned)((units + 7) / 8), 1, split);

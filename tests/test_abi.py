@@ -79,6 +79,12 @@ def test_null_context_errors(lib):
     assert lib._lib.corr_destroy(None) == lib.CORR_OK
 
 
+def test_probe_rejects_bad_sizes_before_touching_the_device(lib):
+    for n_mma, n_cols in ((0, 256), (1 << 21, 256), (16, 64), (16, 192)):
+        assert lib._lib.corr_probe_mma_rate(n_mma, n_cols, None, None, None) == lib.CORR_ERR_ARG
+    assert "n_cols 128 or 256" in lib.corr_last_error()
+
+
 def test_pfb_coeffs_match_the_oracle(lib):
     """The library's host-side PFB prototype filter equals the oracle's independent computation."""
     import numpy as np

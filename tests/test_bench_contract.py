@@ -53,7 +53,7 @@ def test_reference_arm_other_ranks_exit_quietly():
 @pytest.mark.gpu
 def test_native_arm_line():
     line = _run(["--steps", "2", "--warmup", "3", "--e2e-steps", "1", "--fp32-steps", "0", "--i8-steps", "0",
-                 "--no-cpu-baseline"], timeout=900)
+                 "--no-cpu-baseline", "--no-extras"], timeout=900)
     assert BASE_KEYS | {"roofline", "clocks", "gpu_launches"} <= set(line)
     assert line["n_gpus"] == 1 and line["scaling"] == "weak" and line["dtype"] == "e4m3"
     cfg = line["config"]
@@ -62,6 +62,12 @@ def test_native_arm_line():
     roof = line["roofline"]
     assert roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s" and 0 < roof["frac"] < 1.3
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-9
+    # the issue-rate probe: a positive rate, the kernel's share of it below 1 (it cannot beat the
+    # instruction it issues), and the wide instruction at least as fast per flop as the narrow one
+    probe = roof["issue_probe"]
+    assert probe["tflops_n256"] > 0 and probe["tflops_n128"] > 0
+    assert 0 < roof["frac_issue"] < 1.05 and 0 < roof["frac_useful_of_issue_peak"] < roof["frac_issue"]
+    assert probe["tflops_n256"] >= 0.95 * probe["tflops_n128"]
     assert line["gpu_launches"] > 0 and line["gpu_launches_per_step"] == line["gpu_launches"] / 2
     e2e = line["e2e"]
     assert e2e["unit"] == "Tera-CMAC/s" and 0 < e2e["value"] <= line["value"]

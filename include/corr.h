@@ -308,17 +308,33 @@ int corr_profile_read(corr_ctx* ctx, int kernel, double* total_ms, long long* la
  * d_autos    device int64 [n_chans][n_inputs]: the block's autocorrelations are ADDED.
  * Asynchronous on cuda_stream; the caller owns all three buffers.
  *
- * Limit: n_chans * round_up(n_time, 128) * round_up(2 n_inputs, 128) + 16 n_chans n_inputs bytes
- * plus ~16.6 KiB must fit in 64 MiB (e.g. 512 inputs x 4 channels x 8192 samples); larger shapes
- * return CORR_ERR_ARG with a message naming the size. On each device, the first call looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first call
- * before capturing any stream into a CUDA graph. Every call reuses the same array and clears the
- * parts that must start at zero; calls whose work overlaps on the GPU (different streams, or other
- * threads) race on the array and must be serialised by the caller. A device-side wait that times
- * out leaves the block's result incomplete; this entry point has no context to report it through.
+ * Limit: 256 + round_up(16 C N, 256) + round_up(24 C n_tiles, 256) + C round_up(T, 128) round_up(2 N, 128)
+ * bytes must fit in 64 MiB (C = n_chans, N = n_inputs, T = n_time, n_tiles = the number of plan-0 tiles
+ * of one channel, corr_tile_plan(N, 0, NULL, 0): 20 at 512 inputs), e.g. 512 inputs x 7 channels x
+ * 8192 samples; larger shapes return CORR_ERR_ARG with a message naming the size. The device address
+ * of the array is looked up once per CUDA context (the first call in a context, and the first after a
+ * device reset, do it; make that call before capturing any stream into a CUDA graph). Every call reuses
+ * the same array and clears the parts that must start at zero; calls whose work overlaps on the GPU
+ * (different streams, or other threads) race on the array and must be serialised by the caller. A
+ * device-side wait that times out leaves the block's result incomplete and records a code in the
+ * array, which corr_xengine_static_status reads.
  */
 int corr_xengine_static(const void* d_samples, int n_inputs, int n_chans, int n_time, int n_pol, long long* d_cross,
                         long long* d_autos, void* cuda_stream);
+
+/*
+ * corr_xengine_static_status - the error word that the last corr_xengine_static call left in the fixed
+ * array (no counterpart in the paper; allocates nothing): synchronizes cuda_stream, writes the word to
+ * *code (0, or the code of the bounded wait that gave up) and clears it. Returns CORR_ERR_TIMEOUT when
+ * the word was set (the last block's sums are then incomplete), CORR_ERR_ARG for a NULL code.
+ *
+ * corr_xengine_static_selftest_wait - failure-detection self-test of the same word: enqueues the
+ * bounded-wait kernel of corr_selftest_wait, pointed at the fixed array's error word, waiting limit_ms
+ * (1 .. 2000) on a barrier phase that nothing completes; the next corr_xengine_static_status reports
+ * the timeout (code 90). No fault, trap or hang. Allocates nothing.
+ */
+int corr_xengine_static_status(int* code, void* cuda_stream);
+int corr_xengine_static_selftest_wait(int limit_ms, void* cuda_stream);
 
 /*
  * corr_probe_mma_rate - issue-rate probe of the tensor instruction the X-engine is built on. No

@@ -60,6 +60,8 @@ SIGNATURES = [
     ("corr_group_launch", _c_int, [_c_vp, _c_vp]),
     ("corr_group_destroy", _c_int, [_c_vp]),
     ("corr_xengine_static", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),
+    ("corr_xengine_static_status", _c_int, [ctypes.POINTER(ctypes.c_int), _c_vp]),
+    ("corr_xengine_static_selftest_wait", _c_int, [_c_int, _c_vp]),
     ("corr_probe_mma_rate", _c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      _c_vp]),
     ("corr_destroy", _c_int, [_c_vp]),
@@ -293,6 +295,20 @@ def corr_probe_mma_rate(n_mma: int, n_cols: int, stream: int):
     cyc = ctypes.c_double(0.0)
     _check(_lib.corr_probe_mma_rate(n_mma, n_cols, ctypes.byref(tf), ctypes.byref(cyc), stream), "corr_probe_mma_rate")
     return tf.value, cyc.value
+
+
+def corr_xengine_static_status(stream: int) -> int:
+    """The error word the last corr_xengine_static call left (0 if none; a bounded-wait timeout code
+    otherwise), cleared by the call; raises CorrError on a CUDA error."""
+    code = ctypes.c_int(0)
+    rc = _lib.corr_xengine_static_status(ctypes.byref(code), stream)
+    if rc < 0 and rc != CORR_ERR_TIMEOUT:
+        raise CorrError(rc, "corr_xengine_static_status")
+    return code.value
+
+
+def corr_xengine_static_selftest_wait(limit_ms: int, stream: int) -> int:
+    return _check(_lib.corr_xengine_static_selftest_wait(limit_ms, stream), "corr_xengine_static_selftest_wait")
 
 
 def _ptr_array(ptrs):

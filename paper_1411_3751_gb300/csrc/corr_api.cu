@@ -134,16 +134,50 @@ int sm_count() {
   return n;
 }
 
+namespace {
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+std::once_flag g_ctx_fns_once;
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+}  // namespace
+
+unsigned long long context_id() {
+  std::call_once(g_ctx_fns_once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<ctx_get_current_fn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<ctx_get_id_fn>(p);
+    cudaGetLastError();
+  });
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+    // no context is current: bind the current device's primary context (cudaSetDevice creates it)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  }
+  unsigned long long id = 0;
+  return g_ctx_get_id(ctx, &id) == CUDA_SUCCESS ? id : 0;
+}
+
 cudaError_t set_smem_limit(const void* func, int bytes) {
   static std::mutex m;
-  static std::set<std::pair<const void*, int>> done;  // (kernel, device)
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+  static std::set<std::pair<const void*, unsigned long long>> done;  // (kernel, context); the attribute is per context
+  const unsigned long long ctx = context_id();
   std::lock_guard<std::mutex> lock(m);
-  if (done.count({func, dev})) return cudaSuccess;
-  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.insert({func, dev});
+  if (ctx != 0 && done.count({func, ctx})) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && ctx != 0) done.insert({func, ctx});
   return e;
 }
 }  // namespace corr

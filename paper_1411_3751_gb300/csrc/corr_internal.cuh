@@ -156,8 +156,11 @@ cudaError_t launch_requant(const void* d_in, int in_type, int N, int T, int F, i
 // PFB F-engine: int8 ADC frames -> FIR (exact int32) -> 8192-point real FFT -> float2 [N][T][4096] (pfb.cu).
 cudaError_t launch_pfb(const int8_t* d_adc, long long stride, int N, int T, int P, const int* d_h, float2* d_out,
                        cudaStream_t st);
-// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once per (kernel,
-// device); thread-safe.
+// Unique id of the CUDA context current to this thread (binding the device's primary context if none
+// is), or 0 if it cannot be read.
+unsigned long long context_id();
+// Raise a kernel's dynamic shared-memory limit to `bytes` in the current context, once per (kernel,
+// context); thread-safe.
 cudaError_t set_smem_limit(const void* func, int bytes);
 cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, int fmt, long long n_samples,
                         long long k_base, const Shape2& g, cudaStream_t st);

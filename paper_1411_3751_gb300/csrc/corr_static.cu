@@ -8,6 +8,8 @@
 // The caller passes the input block and the output accumulators only.
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "corr_internal.cuh"
@@ -16,18 +18,38 @@ namespace corr {
 namespace {
 
 // One shared scratch array (64 MiB, 256-byte aligned), carved per call as
-//   [0, 256)          error flag of the bounded waits
-//   [256, 256 + 1 MiB) channel-major work list (up to 43690 items)
-//   [.., ...)          offset sums s[C][N][2] int64, then the e4m3 operand op[C][T_pad][R]
+//   [0, 256)                          error word of the bounded waits
+//   [256, 256 + S)                    offset sums s[C][N][2] int64, S = round_up(16 C N, 256)
+//   [.., .. + W)                      channel-major work list, W = round_up(24 C n_tiles, 256)
+//   [.., .. + C T_pad R)              the e4m3 operand op[C][T_pad][R]
 constexpr size_t kStaticScratchBytes = 64ull << 20;
-constexpr size_t kOffItems = 256;
-constexpr long long kMaxItems = (1ll << 20) / sizeof(WorkItem);
-constexpr size_t kOffSums = kOffItems + (1ull << 20);
+constexpr size_t kOffSums = 256;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device (set once)
+// Device address of g_static_scratch, looked up once per CUDA context (a device reset, or another
+// context on the same device, loads the module again at another address), under a lock.
+// Returns nullptr with *err set on failure.
+void* scratch_address(std::string* err) {
+  static std::mutex m;
+  static std::map<unsigned long long, void*> by_context;
+  const unsigned long long id = context_id();
+  if (id == 0) {
+    *err = "the current CUDA context cannot be identified";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(m);
+  const auto it = by_context.find(id);
+  if (it != by_context.end()) return it->second;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return nullptr;
+  }
+  by_context[id] = p;
+  return p;
+}
 
 // Channel-major work list: item w = tile (w mod n_tiles) of channel w / n_tiles, the tiles being the
 // plan-0 enumeration of the context path (a-side spans of 128 inputs, half-width on odd c-blocks).
@@ -102,32 +124,29 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
     return static_fail(CORR_ERR_ARG, "corr_xengine_static: invalid shape");
   const long long R = round_up(2LL * n_inputs, kF8RowAlign);
   const long long T_pad = round_up(n_time, kF8Kt);
+  // tile count is a pure function of N (the context path's plan-0 enumeration, counted on the host)
+  const int n_tiles = (int)f8_tile_plan(n_inputs, (int)R, 0).size();
+  const long long n_items = (long long)n_tiles * n_chans;
   const size_t sums = (size_t)n_chans * n_inputs * 16;
-  const size_t off_op = round_up((long long)(kOffSums + sums), 256);
+  const size_t off_items = kOffSums + (size_t)round_up((long long)sums, 256);
+  const size_t off_op = off_items + (size_t)round_up(n_items * (long long)sizeof(WorkItem), 256);
   const size_t need = off_op + (size_t)n_chans * (size_t)T_pad * (size_t)R;
   if (need > kStaticScratchBytes)
     return static_fail(CORR_ERR_ARG, "corr_xengine_static: needs " + std::to_string(need) +
                                          " bytes of scratch, above the fixed maximum of " +
                                          std::to_string(kStaticScratchBytes) +
-                                         " (C * round_up(T, 128) * round_up(2N, 128) + 16 C N + 16.6 KiB)");
+                                         " (256 + round_up(16 C N, 256) + round_up(24 C n_tiles, 256) + "
+                                         "C round_up(T, 128) round_up(2 N, 128))");
 
-  // Per-device set-up: the device address of the scratch array, once per device.
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return static_fail(CORR_ERR_ARG, "corr_xengine_static: device index too large");
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p)
-      return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: cudaGetSymbolAddress: ") +
-                                            cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  std::string aerr;
+  unsigned char* base = static_cast<unsigned char*>(scratch_address(&aerr));
+  if (!base) return static_fail(CORR_ERR_CUDA, "corr_xengine_static: " + aerr);
   int* d_err = reinterpret_cast<int*>(base);
-  WorkItem* d_items = reinterpret_cast<WorkItem*>(base + kOffItems);
   long long* d_s = reinterpret_cast<long long*>(base + kOffSums);
+  WorkItem* d_items = reinterpret_cast<WorkItem*>(base + off_items);
   uint8_t* d_op = base + off_op;
 
   Shape sh;
@@ -140,12 +159,6 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
   sh.P = n_pol * n_pol;
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
-  // tile count is a pure function of N (the context path's enumeration, counted on the host)
-  const int n_tiles = (int)f8_tile_plan(n_inputs, (int)R, 0).size();
-  const long long n_items = (long long)n_tiles * n_chans;
-  if (n_items > kMaxItems)
-    return static_fail(CORR_ERR_ARG, "corr_xengine_static: " + std::to_string(n_items) +
-                                         " work items, above the fixed maximum of " + std::to_string(kMaxItems));
   CUtensorMap tmap;
   std::string err;
   if (encode_op_tensor_map(&tmap, d_op, (int)R, (int)T_pad, n_chans, &err) != 0)
@@ -190,5 +203,38 @@ extern "C" int corr_xengine_static(const void* d_samples, int n_inputs, int n_ch
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static: ") + cudaGetErrorString(e));
+  return CORR_OK;
+}
+
+extern "C" int corr_xengine_static_status(int* code, void* cuda_stream) {
+  if (!code) return static_fail(CORR_ERR_ARG, "corr_xengine_static_status: NULL code");
+  *code = 0;
+  std::string aerr;
+  unsigned char* base = static_cast<unsigned char*>(scratch_address(&aerr));
+  if (!base) return static_fail(CORR_ERR_CUDA, "corr_xengine_static_status: " + aerr);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, base, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && h != 0) e = cudaMemsetAsync(base, 0, sizeof(int), st);
+  if (e == cudaSuccess && h != 0) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static_status: ") + cudaGetErrorString(e));
+  *code = h;
+  if (h != 0)
+    return static_fail(CORR_ERR_TIMEOUT, "corr_xengine_static_status: a device-side wait timed out (code " +
+                                             std::to_string(h) + ")");
+  return CORR_OK;
+}
+
+extern "C" int corr_xengine_static_selftest_wait(int limit_ms, void* cuda_stream) {
+  if (limit_ms < 1 || limit_ms > 2000)
+    return static_fail(CORR_ERR_ARG, "corr_xengine_static_selftest_wait: limit_ms must be in [1, 2000]");
+  std::string aerr;
+  unsigned char* base = static_cast<unsigned char*>(scratch_address(&aerr));
+  if (!base) return static_fail(CORR_ERR_CUDA, "corr_xengine_static_selftest_wait: " + aerr);
+  const cudaError_t e = launch_wait_selftest(reinterpret_cast<int*>(base), limit_ms, 90, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess)
+    return static_fail(CORR_ERR_CUDA, std::string("corr_xengine_static_selftest_wait: ") + cudaGetErrorString(e));
   return CORR_OK;
 }

@@ -11,8 +11,9 @@ Prints ONE JSON line (rank 0). Metric: useful Tera-CMAC/s = N (N + 1) / 2 * C * 
 the real-time factor at the 24.0 kHz channel rate. `--impl reference` times the CPU oracle instead.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--path fp8tc|i8mma|fp32] [--impl reference]
-Multi-GPU: launched by torch.distributed.run; channels are independent, every rank runs the same
-per-GPU workload on its own GPU (weak scaling), no data-path collective.
+Multi-GPU: launched by torch.distributed.run; channels are independent, so rank r correlates its own
+contiguous 128-channel range (replicas.channel_shards) of a band of 128 x n_gpus channels (weak
+scaling), with no data-path collective.
 """
 from __future__ import annotations
 
@@ -337,8 +338,16 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    spec = synth.Spec(kind="gauss_tone", seed=SEED + 1000 * rank)
-    blocks = [synth.generate_device(spec, T_BLOCK, N_CHAN, N_IN, t0=b * T_BLOCK) for b in range(N_BLOCKS)]
+    # rank r correlates its own contiguous channel range of a band of N_CHAN x world channels (the
+    # paper's partition: each GPU its own channels, no exchange in the X stage); at one GPU the band
+    # is the 128-channel workload itself
+    from paper_1411_3751_gb300 import replicas
+
+    band = N_CHAN * world
+    c0, c1 = replicas.channel_shards(band, world)[rank]
+    spec = synth.Spec(kind="gauss_tone", seed=SEED)
+    blocks = [synth.generate_device(spec, T_BLOCK, band, N_IN, t0=b * T_BLOCK, c_range=(c0, c1))
+              for b in range(N_BLOCKS)]
     torch.cuda.synchronize()
     xc = corr.Correlator(N_IN, N_CHAN, T_BLOCK, N_POL, path=args.path)
     cross_out = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64, device=dev)
@@ -523,7 +532,9 @@ def main():
             "vs_baseline": None, "dtype": {"i8mma": "s8", "fp32": "f32"}.get(args.path, "e4m3"), "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN, "n_time_per_block": T_BLOCK,
                        "blocks_per_step": N_BLOCKS, "n_pol": N_POL, "path": args.path,
-                       "l2": "inputs 8 GiB > L2, no flush needed", "parallelism": "channels per GPU (replicas)"},
+                       "l2": "inputs 8 GiB > L2, no flush needed",
+                       "parallelism": "channel shards: each GPU a contiguous 128-channel range of a 128 x n_gpus-channel band",
+                       "band_channels": N_CHAN * world},
             "real_time_factor": rtf,
             "roofline": roof,
             "kernel_ms_per_step": {"xeng": xeng_ms / args.steps, "unpack": unpack_ms / args.steps,

@@ -252,6 +252,30 @@ int corr_pfb_coeffs(int n_fft, int n_taps, int32_t* h_out);
 int corr_pfb(const int8_t* d_adc, int n_inputs, long long input_stride, long long n_samples, int n_taps,
              const int32_t* d_coeffs, int n_spectra, void* d_out, void* cuda_stream);
 
+/*
+ * Corner turn across GPUs (Sec. 2.3 and Fig. 2: each F-engine board produces every channel of its own
+ * antennas, each X-engine GPU correlates every antenna of its own channels, and the network turns
+ * the data from one grouping to the other). With one process per GPU the turn is an all-to-all
+ * exchange (the caller's collective); these are its two local halves on the device, byte
+ * permutations of uint8 samples with no arithmetic. Asynchronous on cuda_stream; bound arrays are
+ * HOST arrays read during the call.
+ *
+ * corr_corner_turn_pack   d_in [n_time][n_chans][n_local] (this rank's inputs, every channel) ->
+ *                         d_out = for each destination d < n_dest, in order, the contiguous block
+ *                         [n_time][chan_bounds[d + 1] - chan_bounds[d]][n_local] of channels
+ *                         chan_bounds[d] ..; chan_bounds[0] = 0 <= ... <= chan_bounds[n_dest] = n_chans.
+ * corr_corner_turn_unpack d_in = for each source s < n_src, in order, the contiguous block
+ *                         [n_time][n_chans][input_bounds[s + 1] - input_bounds[s]] ->
+ *                         d_out [n_time][n_chans][n_inputs], source s's block at inputs
+ *                         input_bounds[s] ..; input_bounds[0] = 0 <= ... <= input_bounds[n_src] = n_inputs.
+ * CORR_ERR_ARG for NULL buffers, bounds that do not run from 0 to the total without decreasing, or
+ * more than 1024 parts. Device buffers do not overlap; 16-byte-aligned rows are copied as vectors.
+ */
+int corr_corner_turn_pack(const void* d_in, int n_time, int n_chans, int n_local, const int* chan_bounds, int n_dest,
+                          void* d_out, void* cuda_stream);
+int corr_corner_turn_unpack(const void* d_in, int n_time, int n_chans, int n_inputs, const int* input_bounds,
+                            int n_src, void* d_out, void* cuda_stream);
+
 /* Samples per channel accumulated into `what` since creation or its last reset (host-side count). */
 long long corr_samples_accumulated(const corr_ctx* ctx, int what);
 

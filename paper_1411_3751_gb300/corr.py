@@ -43,6 +43,10 @@ SIGNATURES = [
     ("corr_pfb", _c_int, [_c_vp, _c_int, ctypes.c_longlong, ctypes.c_longlong, _c_int, _c_vp, _c_int, _c_vp, _c_vp]),
     ("corr_requantize", _c_int, [_c_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.c_float, _c_vp,
                                  _c_int, _c_vp, _c_vp]),
+    ("corr_corner_turn_pack", _c_int, [_c_vp, _c_int, _c_int, _c_int, ctypes.POINTER(ctypes.c_int), _c_int, _c_vp,
+                                       _c_vp]),
+    ("corr_corner_turn_unpack", _c_int, [_c_vp, _c_int, _c_int, _c_int, ctypes.POINTER(ctypes.c_int), _c_int, _c_vp,
+                                         _c_vp]),
     ("corr_samples_accumulated", _c_ll, [_c_vp, _c_int]),
     ("corr_reset", _c_int, [_c_vp, _c_int, _c_vp]),
     ("corr_sync", _c_int, [_c_vp, _c_vp]),
@@ -239,6 +243,20 @@ def corr_dump_stations(ctx: int, stations, n_stations: int, out: int, is_device_
         stations = ctypes.addressof(arr)
     return _check(_lib.corr_dump_stations(ctx, stations, n_stations, out, is_device_ptr, what, fmt, reset, stream),
                   "corr_dump_stations")
+
+
+def corr_corner_turn_pack(d_in: int, n_time: int, n_chans: int, n_local: int, chan_bounds, d_out: int,
+                          stream: int) -> int:
+    b = (ctypes.c_int * len(chan_bounds))(*[int(v) for v in chan_bounds])
+    return _check(_lib.corr_corner_turn_pack(d_in, n_time, n_chans, n_local, b, len(chan_bounds) - 1, d_out, stream),
+                  "corr_corner_turn_pack")
+
+
+def corr_corner_turn_unpack(d_in: int, n_time: int, n_chans: int, n_inputs: int, input_bounds, d_out: int,
+                            stream: int) -> int:
+    b = (ctypes.c_int * len(input_bounds))(*[int(v) for v in input_bounds])
+    return _check(_lib.corr_corner_turn_unpack(d_in, n_time, n_chans, n_inputs, b, len(input_bounds) - 1, d_out,
+                                               stream), "corr_corner_turn_unpack")
 
 
 def corr_samples_accumulated(ctx: int, what: int) -> int:

@@ -131,6 +131,11 @@ def _lib_cuda():
         lib.synth_generate_device.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_longlong, ctypes.POINTER(SynthParams), ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.synth_generate_device_range.restype = ctypes.c_int
+        lib.synth_generate_device_range.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                                    ctypes.POINTER(SynthParams), ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p]
         _cuda_lib = lib
     return _cuda_lib
 
@@ -168,18 +173,21 @@ def _tables_on_device(spec: Spec, N: int):
     return t
 
 
-def generate_device(spec: Spec, T: int, C: int, N: int, t0: int = 0, out=None, stream=None, sync: bool = True):
-    """torch.uint8 cuda tensor [T][C][N] (written on the given or current stream; sync=False returns
-    without waiting for the kernel)."""
+def generate_device(spec: Spec, T: int, C: int, N: int, t0: int = 0, out=None, stream=None, sync: bool = True,
+                    c_range=None):
+    """torch.uint8 cuda tensor [T][C][N], or [T][c1 - c0][N] holding channels c_range = (c0, c1) of a
+    C-channel array (written on the given or current stream; sync=False returns without waiting for
+    the kernel)."""
     import torch
 
+    cb, cn = (0, C) if c_range is None else (c_range[0], c_range[1] - c_range[0])
     if out is None:
-        out = torch.empty((T, C, N), dtype=torch.uint8, device="cuda")
+        out = torch.empty((T, cn, N), dtype=torch.uint8, device="cuda")
     d_lo, d_hi, d_k = _tables_on_device(spec, N)
     s = stream if stream is not None else torch.cuda.current_stream()
     p = spec.params()
-    rc = _lib_cuda().synth_generate_device(out.data_ptr(), T, C, N, t0, ctypes.byref(p), d_lo.data_ptr(),
-                                           d_hi.data_ptr(), d_k.data_ptr(), int(s.cuda_stream))
+    rc = _lib_cuda().synth_generate_device_range(out.data_ptr(), T, cb, cn, C, N, t0, ctypes.byref(p), d_lo.data_ptr(),
+                                                 d_hi.data_ptr(), d_k.data_ptr(), int(s.cuda_stream))
     if rc != 0:
         raise RuntimeError("synth_generate_device failed: %d" % rc)
     if sync:

@@ -49,16 +49,17 @@ __device__ __forceinline__ uint8_t sample_byte(const synth_params& p, uint64_t L
 
 // One thread per 16 consecutive inputs of one (t, c) row: the row arithmetic is done once per 16
 // samples and the bytes leave as one 16-byte store where the row allows it.
-__global__ void synth_kernel(uint8_t* __restrict__ out, long long rows, int C, int N, long long t0, synth_params p,
-                             const int32_t* __restrict__ tab_lo, const int32_t* __restrict__ tab_hi,
-                             const int32_t* __restrict__ k, bool vec) {
+// Rows cover channels c_begin .. c_begin + c_count - 1 of an array with C channels.
+__global__ void synth_kernel(uint8_t* __restrict__ out, long long rows, int c_begin, int c_count, int C, int N,
+                             long long t0, synth_params p, const int32_t* __restrict__ tab_lo,
+                             const int32_t* __restrict__ tab_hi, const int32_t* __restrict__ k, bool vec) {
   const int chunks = (N + 15) / 16;
   const long long units = rows * chunks;
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < units; w += (long long)gridDim.x * blockDim.x) {
     const long long r = w / chunks;
     const int n0 = (int)(w - r * chunks) * 16;
-    const long long tl = r / C;
-    const int c = (int)(r - tl * C);
+    const long long tl = r / c_count;
+    const int c = c_begin + (int)(r - tl * c_count);
     const long long t = t0 + tl;
     const long long seg = p.profile == SYNTH_UNIFORM ? 0 : t / p.seg_len;
     const uint64_t L0 = ((uint64_t)t * (uint64_t)C + (uint64_t)c) * (uint64_t)N + (uint64_t)n0;
@@ -84,18 +85,24 @@ __global__ void synth_kernel(uint8_t* __restrict__ out, long long rows, int C, i
 
 }  // namespace
 
-extern "C" int synth_generate_device(uint8_t* out, int T, int C, int N, long long t0, const synth_params* p,
-                                     const int32_t* tab_lo, const int32_t* tab_hi, const int32_t* k, void* stream) {
-  if (!out || !p || T < 0 || C < 1 || N < 1) return -1;
+extern "C" int synth_generate_device_range(uint8_t* out, int T, int c_begin, int c_count, int C, int N, long long t0,
+                                           const synth_params* p, const int32_t* tab_lo, const int32_t* tab_hi,
+                                           const int32_t* k, void* stream) {
+  if (!out || !p || T < 0 || C < 1 || N < 1 || c_begin < 0 || c_count < 0 || c_begin + c_count > C) return -1;
   if (p->profile == SYNTH_GAUSS_TONE && (!tab_lo || !k || p->unit_lo <= 2200 || p->unit_lo >= (1 << 25) || p->seg_len <= 0)) return -1;
   if (p->profile == SYNTH_GAUSS_TONE && p->sat_period == 2 && (!tab_hi || p->unit_hi <= 2200 || p->unit_hi >= (1 << 25))) return -1;
-  const long long rows = (long long)T * C;
+  const long long rows = (long long)T * c_count;
   if (rows == 0) return 0;
   const long long units = rows * ((N + 15) / 16);
   long long blocks = (units + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   const bool vec = (N % 16) == 0 && (reinterpret_cast<uintptr_t>(out) % 16) == 0;
-  synth_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(out, rows, C, N, t0, *p, tab_lo,
+  synth_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(out, rows, c_begin, c_count, C, N, t0, *p, tab_lo,
                                                                     tab_hi ? tab_hi : tab_lo, k, vec);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+extern "C" int synth_generate_device(uint8_t* out, int T, int C, int N, long long t0, const synth_params* p,
+                                     const int32_t* tab_lo, const int32_t* tab_hi, const int32_t* k, void* stream) {
+  return synth_generate_device_range(out, T, 0, C, C, N, t0, p, tab_lo, tab_hi, k, stream);
 }

@@ -48,6 +48,12 @@ typedef struct synth_params {
 int synth_generate_device(uint8_t* out, int T, int C, int N, long long t0, const synth_params* p,
                           const int32_t* tab_lo, const int32_t* tab_hi, const int32_t* k, void* stream);
 
+/* Device, a channel range: out = uint8[T][c_count][N] holding channels c_begin .. c_begin + c_count - 1
+ * of an array with C channels (the same bytes as those channels of synth_generate_device's output). */
+int synth_generate_device_range(uint8_t* out, int T, int c_begin, int c_count, int C, int N, long long t0,
+                                const synth_params* p, const int32_t* tab_lo, const int32_t* tab_hi,
+                                const int32_t* k, void* stream);
+
 /* Host: out = uint8[t_count][c_count][N] holding times t0 + t_begin .. and channels c_begin ..
  * of an array with C channels; host pointers. Returns 0 or -1. */
 int synth_generate_host(uint8_t* out, int t_begin, int t_count, int c_begin, int c_count, int C, int N,

@@ -79,6 +79,17 @@ def test_null_context_errors(lib):
     assert lib._lib.corr_destroy(None) == lib.CORR_OK
 
 
+def test_corner_turn_rejects_bad_bounds_before_touching_the_device(lib):
+    import ctypes
+
+    fake = ctypes.c_void_p(16)
+    for bounds in ([0, 3], [1, 4], [0, 3, 2, 4], [0]):
+        b = (ctypes.c_int * len(bounds))(*bounds)
+        assert lib._lib.corr_corner_turn_pack(fake, 2, 4, 8, b, len(bounds) - 1, fake, None) == lib.CORR_ERR_ARG
+        assert lib._lib.corr_corner_turn_unpack(fake, 2, 3, 4, b, len(bounds) - 1, fake, None) == lib.CORR_ERR_ARG
+    assert "bounds" in lib.corr_last_error()
+
+
 def test_probe_rejects_bad_sizes_before_touching_the_device(lib):
     for n_mma, n_cols in ((0, 256), (1 << 21, 256), (16, 64), (16, 192)):
         assert lib._lib.corr_probe_mma_rate(n_mma, n_cols, None, None, None) == lib.CORR_ERR_ARG

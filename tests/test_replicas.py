@@ -108,3 +108,64 @@ def test_a_dead_replica_is_detected_at_the_next_barrier():
                 p.kill()
     assert status == "detected" and waited < 60, (status, waited)
     assert procs[1].exitcode == 3
+
+
+def test_input_shards_are_whole_stations():
+    assert replicas.input_shards(512, 22, 2)[0] == (0, 24)
+    for N, W, P in ((512, 2, 2), (512, 3, 2), (12, 5, 2), (7, 3, 1), (4, 8, 2)):
+        sh = replicas.input_shards(N, W, P)
+        assert len(sh) == W and sh[0][0] == 0 and sh[-1][1] == N
+        assert all(a[1] == b[0] for a, b in zip(sh, sh[1:])) and all((b - a) % P == 0 for a, b in sh)
+    with pytest.raises(ValueError):
+        replicas.input_shards(7, 2, 2)
+
+
+def _turn_worker(rank, world, port, q, N, C, T, npol):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    import torch
+    import torch.distributed as dist
+
+    from oracle import oracle
+    from paper_1411_3751_gb300 import synth
+
+    w, r, _ = replicas.init("gloo", timeout_s=60)
+    # this rank's F-engine output: every channel of its own inputs
+    n0, n1 = replicas.input_shards(N, w, npol)[r]
+    full = synth.generate_host(synth.Spec(kind="gauss_tone", seed=1411), T, C, N)
+    x_local = torch.from_numpy(np.ascontiguousarray(full[:, :, n0:n1]))
+    shard = replicas.corner_turn(x_local, N, w, r, npol).numpy()
+    c0, c1 = replicas.channel_shards(C, w)[r]
+    cross, autos = oracle.correlate(shard, npol)
+    got = [None] * w
+    dist.all_gather_object(got, (c0, c1, shard, cross, autos))
+    if r == 0:
+        q.put(got)
+    replicas.finalize(w)
+
+
+@pytest.mark.parametrize("world,N,C,T,npol", [(2, 12, 11, 64, 2), (3, 10, 7, 40, 2), (3, 9, 5, 33, 1)])
+def test_corner_turn_then_correlate_reassembles_the_band(world, N, C, T, npol):
+    """gloo ranks on CPU, each holding every channel of its own inputs (an F-engine's output, Sec. 2.3):
+    after the all-to-all corner turn each holds every input of its own channels, correlates them with
+    the oracle, and the shards reassemble bit-exactly into the single-process result; uneven input and
+    channel shards included."""
+    import torch.multiprocessing as mp
+
+    from oracle import oracle
+    from paper_1411_3751_gb300 import synth
+
+    oracle.build()
+    synth._lib_host()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    mp.start_processes(_turn_worker, args=(world, _free_port(), q, N, C, T, npol), nprocs=world, join=True,
+                       start_method="spawn")
+    got = q.get(timeout=60)
+    full = synth.generate_host(synth.Spec(kind="gauss_tone", seed=1411), T, C, N)
+    want_c, want_a = oracle.correlate(full, npol)
+    assert [g[:2] for g in got] == replicas.channel_shards(C, world)
+    for c0, c1, shard, _, _ in got:
+        assert np.array_equal(shard, full[:, c0:c1, :])
+    assert np.array_equal(np.concatenate([g[3] for g in got]), want_c)
+    assert np.array_equal(np.concatenate([g[4] for g in got]), want_a)

@@ -317,6 +317,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the flush-overhead, grouped-launch, streaming and small-array measurements")
     ap.add_argument("--no-probe", action="store_true", help="skip the tcgen05 issue-rate probe")
+    ap.add_argument("--prep-sms", type=int, default=-1,
+                    help="SMs building the next launch's operand beside the X-engine (-1 library default, 0 none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -350,6 +352,7 @@ def main():
               for b in range(N_BLOCKS)]
     torch.cuda.synchronize()
     xc = corr.Correlator(N_IN, N_CHAN, T_BLOCK, N_POL, path=args.path)
+    xc.set_prep_sms(args.prep_sms)
     cross_out = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64, device=dev)
     autos_out = torch.empty(xc.out_shape(corr.CORR_WHAT_AUTO), dtype=torch.int64, device=dev)
 
@@ -416,6 +419,15 @@ def main():
         peak_note = "FP32 FMA microbenchmark (152 SMs x 128 lanes x 2 flop)"
         bound = "alu"
     achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
+    # with overlapped batches the X-engine shares the GPU with the operand build: all launches but
+    # the last of each batch run on SMs - prep_sms SMs
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    prep_sms = xc.prep_sms if args.path == "fp8tc" else 0
+    launches_per_batch = max(1, round(xeng_n / args.steps))
+    if prep_sms > 0 and launches_per_batch > 1:
+        sm_share = ((launches_per_batch - 1) * (n_sms - prep_sms) + n_sms) / (launches_per_batch * n_sms)
+    else:
+        sm_share = 1.0
     traffic = None
     if args.path == "fp8tc":
         traffic = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch)
@@ -424,7 +436,8 @@ def main():
                                            "i8mma": "xeng_i8mma_kernel"}.get(args.path, "xeng_fp32_kernel"),
             "peak_source": peak_note, "launch_ms": per_launch_ms,
             "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop (%.0f blocks of 8192 samples per launch)"
-                           % (flops_launch, blocks_per_launch)}
+                           % (flops_launch, blocks_per_launch),
+            "sm_share": sm_share, "frac_of_sms_held": achieved / peak / sm_share}
     if args.path.startswith("fp8tc") and probe:
         # the same kernel against the tcgen05 issue rate measured on this GPU just before the timed
         # region: the ideal launch time of the MMAs the tile plan issues, and the useful rate's share
@@ -532,6 +545,7 @@ def main():
             "vs_baseline": None, "dtype": {"i8mma": "s8", "fp32": "f32"}.get(args.path, "e4m3"), "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN, "n_time_per_block": T_BLOCK,
                        "blocks_per_step": N_BLOCKS, "n_pol": N_POL, "path": args.path,
+                       "prep_sms": prep_sms,
                        "l2": "inputs 8 GiB > L2, no flush needed",
                        "parallelism": "channel shards: each GPU a contiguous 128-channel range of a 128 x n_gpus-channel band",
                        "band_channels": N_CHAN * world},

@@ -131,6 +131,21 @@ int corr_get_tile_plan(const corr_ctx* ctx);
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
 
 /*
+ * corr_set_prep_sms - how corr_accumulate_batch schedules the two passes of the tensor path (Sec. 2.4's
+ * unpack ahead of Sec. 2.5's cross-multiply). With sms > 0, a batch of more than one launch builds the
+ * operand of launch j + 1 on `sms` SMs (a TMA-fed build kernel on an internal stream) while the
+ * X-engine multiplies launch j on the other SMs; the first build and the last multiply use the whole
+ * GPU. The first such batch allocates a second operand buffer of the first one's size (see
+ * corr_footprint_bytes); if that fails, or the shape does not suit the TMA build (n_inputs % 16 != 0,
+ * n_inputs < 128, T < 128, a tile plan of 2, or a block not 16-byte aligned), batches run the two
+ * passes in sequence. 0 runs them in sequence always; -1 (the default) picks a fifth of the SMs.
+ * Results are identical either way. CORR_ERR_ARG outside -1 .. SMs - 1. corr_get_prep_sms returns the
+ * SM count in use (the automatic value resolved).
+ */
+int corr_set_prep_sms(corr_ctx* ctx, int sms);
+int corr_get_prep_sms(const corr_ctx* ctx);
+
+/*
  * corr_set_flush_period - maximum number of samples accumulated in on-chip FP32/int32 partial sums
  * before they are added to the int64 accumulators (the paper integrates 8000-spectrum groups and
  * then sums 27 of them, Sec. 2.5; the flush cadence is this library's choice). 0 restores the
@@ -296,7 +311,9 @@ int corr_selftest_wait(corr_ctx* ctx, int limit_ms, void* cuda_stream);
 int corr_sync(corr_ctx* ctx, void* cuda_stream);
 
 /* Device bytes corr_create(n_inputs, n_chans, n_time_per_block, n_pol) allocates for `path`
- * (accumulators + path scratch + staging), or 0 for invalid arguments. */
+ * (accumulators + path scratch + staging), or 0 for invalid arguments. An overlapped batch (see
+ * corr_set_prep_sms) allocates one more operand buffer on first use: the footprint of CORR_PATH_FP8TC
+ * minus that of CORR_PATH_FP32. */
 size_t corr_footprint_bytes(int n_inputs, int n_chans, int n_time_per_block, int n_pol, int path);
 
 /* Number of station pairs B_s = S (S + 1) / 2 for n_inputs / n_pol stations (0 if invalid). */

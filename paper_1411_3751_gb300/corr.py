@@ -32,6 +32,8 @@ SIGNATURES = [
     ("corr_set_tile_plan", _c_int, [_c_vp, _c_int]),
     ("corr_get_tile_plan", _c_int, [_c_vp]),
     ("corr_tile_plan", _c_int, [_c_int, _c_int, _c_vp, _c_int]),
+    ("corr_set_prep_sms", _c_int, [_c_vp, _c_int]),
+    ("corr_get_prep_sms", _c_int, [_c_vp]),
     ("corr_set_flush_period", _c_int, [_c_vp, _c_int]),
     ("corr_accumulate", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_accumulate_batch", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_vp]),
@@ -132,6 +134,14 @@ def corr_tile_plan(n_inputs: int, plan: int):
     buf = (ctypes.c_int * (4 * max(n, 1)))()
     _check(_lib.corr_tile_plan(n_inputs, plan, buf, n), "corr_tile_plan")
     return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
+
+
+def corr_set_prep_sms(ctx: int, sms: int) -> int:
+    return _check(_lib.corr_set_prep_sms(ctx, sms), "corr_set_prep_sms")
+
+
+def corr_get_prep_sms(ctx: int) -> int:
+    return _check(_lib.corr_get_prep_sms(ctx), "corr_get_prep_sms")
 
 
 def corr_set_flush_period(ctx: int, n_samples: int) -> int:
@@ -408,6 +418,14 @@ class Correlator:
 
     def set_flush_period(self, n: int):
         corr_set_flush_period(self.ctx, n)
+
+    def set_prep_sms(self, sms: int):
+        """SMs that build the next launch's operand beside the X-engine in batches (-1 auto, 0 none)."""
+        corr_set_prep_sms(self.ctx, sms)
+
+    @property
+    def prep_sms(self) -> int:
+        return corr_get_prep_sms(self.ctx)
 
     def set_tile_plan(self, plan: int):
         """Work-item plan of the two-pass tensor path (0 default, 1, 2: c-block pairs)."""

@@ -261,6 +261,13 @@ void free_ctx(corr_ctx* c) {
     if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
   }
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  cudaFree(c->d_op2);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_op_ready[k]) cudaEventDestroy(c->ev_op_ready[k]);
+    if (c->ev_op_free[k]) cudaEventDestroy(c->ev_op_free[k]);
+  }
+  if (c->ev_batch_start) cudaEventDestroy(c->ev_batch_start);
+  if (c->prep_stream) cudaStreamDestroy(c->prep_stream);
   delete c;
 }
 
@@ -371,6 +378,7 @@ int ensure_operand_scratch(corr_ctx* c) {
     c->d_op = nullptr;
     return fail(CORR_ERR_OOM, "operand scratch allocation failed");
   }
+  c->smap_ok[0] = false;
   cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_buf_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
   std::string err;
@@ -382,6 +390,92 @@ int ensure_operand_scratch(corr_ctx* c) {
   return CORR_OK;
 }
 
+// SMs that build the next chunk's operand while the X-engine multiplies the current one.
+int prep_sms_for(const corr_ctx* c) {
+  if (c->prep_sms >= 0) return c->prep_sms;
+  return c->num_sms / 5;  // automatic: a fifth of the SMs
+}
+
+// The second operand buffer, the TMA store maps of both buffers, and the stream and events of
+// overlapped batches (allocated on first use).
+int ensure_overlap(corr_ctx* c) {
+  std::string err;
+  if (!c->d_op2) {
+    if (cudaMalloc(&c->d_op2, c->L.op_buf_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_op2 = nullptr;
+      return fail(CORR_ERR_OOM, "second operand buffer allocation failed");
+    }
+    cudaError_t e = cudaMemset(c->d_op2, 0, c->L.op_buf_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "second operand buffer init");
+    if (encode_op_tensor_map(&c->tmap2, c->d_op2, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
+      cudaFree(c->d_op2);
+      c->d_op2 = nullptr;
+      return fail(CORR_ERR_CUDA, err);
+    }
+    c->smap_ok[1] = false;
+  }
+  for (int b = 0; b < 2; ++b)
+    if (!c->smap_ok[b]) {
+      if (encode_op_store_map(&c->smap[b], b ? c->d_op2 : c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C,
+                              &err) != 0)
+        return fail(CORR_ERR_CUDA, err);
+      c->smap_ok[b] = true;
+    }
+  if (!c->prep_stream) {
+    bool ok = cudaStreamCreateWithFlags(&c->prep_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+      ok = cudaEventCreateWithFlags(&c->ev_op_ready[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->ev_op_free[k], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&c->ev_batch_start, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_fail(cudaGetLastError(), "overlap stream / events");
+  }
+  return CORR_OK;
+}
+
+// n blocks in chunks of K_batch blocks, the operand build of chunk j + 1 overlapping the multiply of
+// chunk j: the build runs with TMA on k SMs on the context's build stream into one operand buffer
+// while the X-engine multiplies the other buffer on the remaining SMs on the caller's stream; events
+// order each buffer's reuse. The first build and the last multiply have the GPU to themselves.
+int accumulate_batch_overlap(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st, int k) {
+  const int T_blk = c->L.s.T;
+  const int T_pad = c->L.T_pad;
+  const int K = c->L.K_batch;
+  const int flush = flush_for(c, CORR_PATH_FP8TC);
+  const int S = c->num_sms;
+  const int rc = ensure_overlap(c);
+  if (rc != CORR_OK) return rc;
+  cudaStream_t ps = c->prep_stream;
+  cudaError_t e = cudaEventRecord(c->ev_batch_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, c->ev_batch_start, 0);
+  const int J = (n + K - 1) / K;
+  for (int j = 0; j < J && e == cudaSuccess; ++j) {
+    const int buf = j & 1;
+    const int b0 = j * K;
+    const int nb = (n - b0) < K ? (n - b0) : K;
+    if (j >= 2) e = cudaStreamWaitEvent(ps, c->ev_op_free[buf], 0);
+    const int grid_p = j == 0 ? S : k;
+    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+      const bool tb = timer_begin(c, CORR_KERNEL_UNPACK, ps);
+      e = launch_f8_prep_tma(c->L.s, blocks[b0 + i], T_blk, T_pad, i * T_pad, c->smap[buf], c->d_soff, c->d_soff_auto,
+                             c->d_err, grid_p, ps);
+      timer_end(c, CORR_KERNEL_UNPACK, ps, tb);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_op_ready[buf], ps);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_op_ready[buf], 0);
+    if (e == cudaSuccess) {
+      const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
+      e = launch_f8_xeng(xeng_args(c, buf ? c->tmap2 : c->tmap, nb * T_pad, flush), j == J - 1 ? S : S - k, st);
+      timer_end(c, CORR_KERNEL_XENG, st, tb);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_op_free[buf], st);
+    c->n_off += (long long)T_blk * nb;
+    c->n_off_auto += (long long)T_blk * nb;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "overlapped batch");
+  return CORR_OK;
+}
+
 // n blocks through the two-pass tensor path in chunks of up to K_batch blocks (launch length from the
 // L2 budget, see kL2Window): the operand of a chunk is built with each block at its own sample
 // offset, then one tensor-core launch multiplies the whole chunk, so blocks share launches and
@@ -389,6 +483,17 @@ int ensure_operand_scratch(corr_ctx* c) {
 // persistent X-engine holds every SM, and inside it the extra load/store traffic slows its epilogue;
 // the chunks run in order on the caller's stream.)
 int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
+  // overlapped schedule when there are at least two chunks and the TMA build takes the shape
+  const int k = prep_sms_for(c);
+  if (k > 0 && k < c->num_sms && n > c->L.K_batch && c->tile_plan != 2) {
+    bool ok = true;
+    for (int b = 0; b < n && ok; ++b) ok = f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
+    if (ok) {
+      const int rc = accumulate_batch_overlap(c, blocks, n, st, k);
+      if (rc != CORR_ERR_OOM) return rc;
+      cudaGetLastError();  // no room for the second buffer: the sequential schedule below
+    }
+  }
   const int T_blk = c->L.s.T;
   const int T_pad = c->L.T_pad;
   const int K = c->L.K_batch;
@@ -470,6 +575,7 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
   }
   c->L = L;
   c->path = CORR_PATH_AUTO;
+  c->prep_sms = -1;
   c->device = dev;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (c->num_sms < 1) c->num_sms = 1;
@@ -548,6 +654,16 @@ int corr_set_tile_plan(corr_ctx* c, int plan) {
 }
 
 int corr_get_tile_plan(const corr_ctx* c) { return c ? c->tile_plan : CORR_ERR_ARG; }
+
+int corr_set_prep_sms(corr_ctx* c, int sms) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_set_prep_sms: NULL context");
+  if (sms < -1 || sms >= c->num_sms)
+    return fail(CORR_ERR_ARG, "corr_set_prep_sms: need -1 (automatic), 0 (no overlap) or 1 .. SMs - 1");
+  c->prep_sms = sms;
+  return CORR_OK;
+}
+
+int corr_get_prep_sms(const corr_ctx* c) { return c ? prep_sms_for(c) : CORR_ERR_ARG; }
 
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles) {
   if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 2 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))

@@ -52,6 +52,15 @@ struct corr_ctx {
   int* d_err;
   uint8_t* d_op;          // operand scratch of the two-pass tensor path (K_batch blocks)
   CUtensorMap tmap;
+  // overlapped batches: the operand of chunk j + 1 is built on prep_sms SMs (TMA build kernel, on
+  // prep_stream) while the X-engine multiplies chunk j on the others; d_op2 is the second buffer
+  int prep_sms;           // -1: automatic, 0: no overlap
+  uint8_t* d_op2;
+  CUtensorMap tmap2;
+  CUtensorMap smap[2];    // store maps of d_op, d_op2 for the TMA build
+  bool smap_ok[2];
+  cudaStream_t prep_stream;
+  cudaEvent_t ev_op_ready[2], ev_op_free[2], ev_batch_start;
   int2* d_tiles32;
   int n_tiles32;
   corr::F8Tile* d_tiles8;        // tile list (current plan), used by the fused path

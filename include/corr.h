@@ -283,8 +283,10 @@ int corr_pfb(const int8_t* d_adc, int n_inputs, long long input_stride, long lon
  *                         [n_time][n_chans][input_bounds[s + 1] - input_bounds[s]] ->
  *                         d_out [n_time][n_chans][n_inputs], source s's block at inputs
  *                         input_bounds[s] ..; input_bounds[0] = 0 <= ... <= input_bounds[n_src] = n_inputs.
- * CORR_ERR_ARG for NULL buffers, bounds that do not run from 0 to the total without decreasing, or
- * more than 1024 parts. Device buffers do not overlap; 16-byte-aligned rows are copied as vectors.
+ * An empty shard (no samples, channels or inputs) moves nothing and may pass NULL buffers.
+ * CORR_ERR_ARG for negative sizes, NULL buffers of a non-empty shard, bounds that do not run from 0 to
+ * the total without decreasing, or more than 1024 parts. Device buffers do not overlap;
+ * 16-byte-aligned rows are copied as vectors.
  */
 int corr_corner_turn_pack(const void* d_in, int n_time, int n_chans, int n_local, const int* chan_bounds, int n_dest,
                           void* d_out, void* cuda_stream);

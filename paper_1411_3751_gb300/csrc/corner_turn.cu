@@ -105,15 +105,15 @@ using namespace corr;
 
 extern "C" int corr_corner_turn_pack(const void* d_in, int n_time, int n_chans, int n_local, const int* chan_bounds,
                                      int n_dest, void* d_out, void* cuda_stream) {
-  if (!d_in || !d_out) return ct_fail(CORR_ERR_ARG, "corr_corner_turn_pack: NULL buffer");
-  if (n_time < 0 || n_chans < 1 || n_local < 1)
-    return ct_fail(CORR_ERR_ARG, "corr_corner_turn_pack: need n_time >= 0, n_chans >= 1, n_local >= 1");
+  if (n_time < 0 || n_chans < 0 || n_local < 0)
+    return ct_fail(CORR_ERR_ARG, "corr_corner_turn_pack: need n_time, n_chans, n_local >= 0");
   Bounds bd;
   if (!read_bounds(chan_bounds, n_dest, n_chans, &bd))
     return ct_fail(CORR_ERR_ARG, "corr_corner_turn_pack: chan_bounds must run 0 = b[0] <= ... <= b[n_dest] = n_chans, "
                                  "1 <= n_dest <= 1024");
   const long long rows = (long long)n_time * n_chans;
-  if (rows == 0) return CORR_OK;
+  if (rows == 0 || n_local == 0) return CORR_OK;  // nothing to move (an empty shard)
+  if (!d_in || !d_out) return ct_fail(CORR_ERR_ARG, "corr_corner_turn_pack: NULL buffer");
   const bool vec = n_local % 16 == 0 && reinterpret_cast<uintptr_t>(d_in) % 16 == 0 &&
                    reinterpret_cast<uintptr_t>(d_out) % 16 == 0;
   ct_pack_kernel<<<grid_for(rows), 256, 0, (cudaStream_t)cuda_stream>>>(static_cast<const uint8_t*>(d_in), n_time,
@@ -126,15 +126,15 @@ extern "C" int corr_corner_turn_pack(const void* d_in, int n_time, int n_chans, 
 
 extern "C" int corr_corner_turn_unpack(const void* d_in, int n_time, int n_chans, int n_inputs, const int* input_bounds,
                                        int n_src, void* d_out, void* cuda_stream) {
-  if (!d_in || !d_out) return ct_fail(CORR_ERR_ARG, "corr_corner_turn_unpack: NULL buffer");
-  if (n_time < 0 || n_chans < 1 || n_inputs < 1)
-    return ct_fail(CORR_ERR_ARG, "corr_corner_turn_unpack: need n_time >= 0, n_chans >= 1, n_inputs >= 1");
+  if (n_time < 0 || n_chans < 0 || n_inputs < 0)
+    return ct_fail(CORR_ERR_ARG, "corr_corner_turn_unpack: need n_time, n_chans, n_inputs >= 0");
   Bounds bd;
   if (!read_bounds(input_bounds, n_src, n_inputs, &bd))
     return ct_fail(CORR_ERR_ARG, "corr_corner_turn_unpack: input_bounds must run 0 = b[0] <= ... <= b[n_src] = "
                                  "n_inputs, 1 <= n_src <= 1024");
   const long long rows = (long long)n_time * n_chans;
-  if (rows == 0) return CORR_OK;
+  if (rows == 0 || n_inputs == 0) return CORR_OK;  // nothing to move (an empty shard)
+  if (!d_in || !d_out) return ct_fail(CORR_ERR_ARG, "corr_corner_turn_unpack: NULL buffer");
   bool vec = n_inputs % 16 == 0 && reinterpret_cast<uintptr_t>(d_in) % 16 == 0 &&
              reinterpret_cast<uintptr_t>(d_out) % 16 == 0;
   for (int s = 0; s <= n_src; ++s) vec = vec && input_bounds[s] % 16 == 0;

@@ -454,11 +454,14 @@ int accumulate_batch_overlap(corr_ctx* c, const uint8_t* const* blocks, int n, c
     const int b0 = j * K;
     const int nb = (n - b0) < K ? (n - b0) : K;
     if (j >= 2) e = cudaStreamWaitEvent(ps, c->ev_op_free[buf], 0);
-    const int grid_p = j == 0 ? S : k;
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
       const bool tb = timer_begin(c, CORR_KERNEL_UNPACK, ps);
-      e = launch_f8_prep_tma(c->L.s, blocks[b0 + i], T_blk, T_pad, i * T_pad, c->smap[buf], c->d_soff, c->d_soff_auto,
-                             c->d_err, grid_p, ps);
+      if (j == 0)  // nothing to overlap with yet: the whole-GPU build
+        e = launch_f8_prep(c->L.s, blocks[b0 + i], T_blk, T_pad, T_pad * K, i * T_pad, c->L.R_buf,
+                           buf ? c->d_op2 : c->d_op, c->d_soff, c->d_soff_auto, ps);
+      else
+        e = launch_f8_prep_tma(c->L.s, blocks[b0 + i], T_blk, T_pad, i * T_pad, c->smap[buf], c->d_soff,
+                               c->d_soff_auto, c->d_err, k, ps);
       timer_end(c, CORR_KERNEL_UNPACK, ps, tb);
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_op_ready[buf], ps);

@@ -1,6 +1,7 @@
 """Profiling driver: a few accumulate calls on one synthetic workload, for `ncu -k <kernel> -s/-c`.
 
     python -m paper_1411_3751_gb300.profile_case --n 512 --c 128 --t 8192 --blocks 3 --path fp8tc
+    python -m paper_1411_3751_gb300.profile_case --n 512 --c 32 --t 8192 --blocks 8 --batch --prep-sms 30
     python -m paper_1411_3751_gb300.profile_case --requant --n 512 --c 2398 --t 256 --blocks 3
     python -m paper_1411_3751_gb300.profile_case --pfb --n 512 --t 16 --blocks 3
 
@@ -26,6 +27,8 @@ def main(argv=None):
     ap.add_argument("--batch", action="store_true",
                     help="accumulate the block --blocks times in one corr_accumulate_batch call (the blocks "
                          "then share tensor-core launches, as in the benchmark)")
+    ap.add_argument("--prep-sms", type=int, default=-1,
+                    help="SMs of the overlapped operand build in batches (-1 library default, 0 sequential)")
     ap.add_argument("--pfb", action="store_true",
                     help="profile the PFB instead: --n inputs x --t spectra, 4 taps")
     ap.add_argument("--requant", action="store_true",
@@ -65,6 +68,7 @@ def main(argv=None):
         return
     x = synth.generate_device(synth.Spec(kind="gauss_tone", seed=a.seed), a.t, a.c, a.n)
     with corr.Correlator(a.n, a.c, a.t, a.npol, path=a.path) as xc:
+        xc.set_prep_sms(a.prep_sms)
         if a.batch:
             xc.accumulate_batch([x] * a.blocks)
         else:

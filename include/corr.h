@@ -132,15 +132,17 @@ int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
 
 /*
  * corr_set_prep_sms - how corr_accumulate_batch schedules the two passes of the tensor path (Sec. 2.4's
- * unpack ahead of Sec. 2.5's cross-multiply). With sms > 0, a batch of more than one launch builds the
- * operand of launch j + 1 on `sms` SMs (a TMA-fed build kernel on an internal stream) while the
- * X-engine multiplies launch j on the other SMs; the first build and the last multiply use the whole
- * GPU. The first such batch allocates a second operand buffer of the first one's size (see
+ * unpack ahead of Sec. 2.5's cross-multiply). With 0 < sms < SMs, a batch of more than one launch
+ * builds the operand of launch j + 1 on `sms` SMs of its own (a TMA-fed build kernel on an internal
+ * stream) while the X-engine multiplies launch j on the other SMs; with sms == SMs a small build CTA
+ * runs beside the X-engine on every SM. The first build and the last multiply use the whole GPU. The
+ * first such batch allocates a second operand buffer of the first one's size (see
  * corr_footprint_bytes); if that fails, or the shape does not suit the TMA build (n_inputs % 16 != 0,
  * n_inputs < 128, T < 128, a tile plan of 2, or a block not 16-byte aligned), batches run the two
- * passes in sequence. 0 runs them in sequence always; -1 (the default) picks a fifth of the SMs.
- * Results are identical either way. CORR_ERR_ARG outside -1 .. SMs - 1. corr_get_prep_sms returns the
- * SM count in use (the automatic value resolved).
+ * passes in sequence. 0 runs them in sequence always; -1 (the default) is the automatic choice, which
+ * on GB300 is 0: the X-engine saturates each SM's memory paths and a concurrent build slows it by more
+ * than the build's own time. Results are identical either way. CORR_ERR_ARG outside -1 .. SMs.
+ * corr_get_prep_sms returns the SM count in use (the automatic value resolved).
  */
 int corr_set_prep_sms(corr_ctx* ctx, int sms);
 int corr_get_prep_sms(const corr_ctx* ctx);

@@ -57,8 +57,6 @@ struct corr_ctx {
   int prep_sms;           // -1: automatic, 0: no overlap
   uint8_t* d_op2;
   CUtensorMap tmap2;
-  CUtensorMap smap[2];    // store maps of d_op, d_op2 for the TMA build
-  bool smap_ok[2];
   cudaStream_t prep_stream;
   cudaEvent_t ev_op_ready[2], ev_op_free[2], ev_batch_start;
   int2* d_tiles32;

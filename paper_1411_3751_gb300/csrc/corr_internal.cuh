@@ -127,12 +127,12 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
 // The same operand bytes and offset sums built with TMA loads and stores by at most max_ctas persistent
 // CTAs (one per SM), for running beside the X-engine (prep_tma.cu); f8_prep_tma_supported says whether
 // the shape and buffer allow it (N % 16 == 0, N >= 128, T_blk >= 128, 16-byte aligned input).
-cudaError_t launch_f8_prep_tma(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int t_base,
-                               const CUtensorMap& op_store_map, long long* d_s1, long long* d_s2, int* d_err,
-                               int max_ctas, cudaStream_t st);
+// beside_xeng: the small variant (about 30 KB of shared memory) that fits next to an X-engine CTA on
+// every SM; otherwise the wide variant for a few SMs of its own.
+cudaError_t launch_f8_prep_tma(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int t_base, uint8_t* d_op,
+                               long long T_span, int R_buf, long long* d_s1, long long* d_s2, int* d_err,
+                               int max_ctas, bool beside_xeng, cudaStream_t st);
 bool f8_prep_tma_supported(const Shape& s, const void* d_in, int T_blk);
-// Store map of an operand buffer op[C][T_span][R] for launch_f8_prep_tma.
-int encode_op_store_map(CUtensorMap* map, void* d_op, int R, int T_span, int C, std::string* err);
 
 // Offset-domain products of every work item into its array's cross sums, diagonal into its autos.
 cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st);

@@ -50,7 +50,8 @@ def test_overlapped_batch_matches_oracle_and_sequential(env, shape):
     want_c, want_a = oracle.correlate(host, npol, threads=8)
     seq_c, seq_a, _ = _batch(env, blocks, N, C, T, npol, 0)
     assert np.array_equal(seq_c, want_c) and np.array_equal(seq_a, want_a)
-    for sms in (1, 8, 30, 76, 151):
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for sms in (1, 8, 30, 76, n_sms - 1, n_sms):  # n_sms: a small build CTA beside the X-engine on every SM
         c, a, _ = _batch(env, blocks, N, C, T, npol, sms)
         bad = np.argwhere(c != want_c)
         assert bad.size == 0, (sms, bad[:3].tolist())
@@ -97,9 +98,10 @@ def test_overlap_then_single_blocks_and_dumps_in_order(env):
 
 
 def test_prep_sms_bounds(env):
-    corr, _, _ = env
+    corr, _, torch = env
     with corr.Correlator(128, 1, 256, 2) as xc:
-        assert xc.prep_sms > 0  # automatic
+        assert xc.prep_sms == 0  # automatic: sequential
+        assert xc.set_prep_sms(torch.cuda.get_device_properties(0).multi_processor_count) is None
         for bad in (-2, 100000):
             with pytest.raises(corr.CorrError):
                 xc.set_prep_sms(bad)

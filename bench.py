@@ -116,17 +116,19 @@ def run_extras():
     return out
 
 
-def issued_flops_per_sample(n_inputs, n_chans):
-    """MMA flops the tensor path issues per sample (tile plan 0: 128 x nb x 32 instructions), split
-    into wide (N = 256) and narrow (N = 128) instructions."""
+def issued_flops_per_sample(n_inputs, n_chans, plan=0):
+    """MMA flops the tensor path issues per sample under a tile plan (M = 128 instructions of N = nb
+    columns; plan 2 items carry a second half of nb1 = extra & 0xFFFF columns), split into wide
+    (N = 256) and narrow (N <= 128) instructions."""
     from paper_1411_3751_gb300 import corr
 
     wide = narrow = 0
-    for _c0, _a0, nb, _x in corr.corr_tile_plan(n_inputs, 0):
-        if nb > 128:
-            wide += 2 * 128 * nb * n_chans
-        else:
-            narrow += 2 * 128 * nb * n_chans
+    for _c0, _a0, nb, extra in corr.corr_tile_plan(n_inputs, plan):
+        for n in (nb, (extra & 0xFFFF) if plan == 2 else 0):
+            if n > 128:
+                wide += 2 * 128 * n * n_chans
+            elif n > 0:
+                narrow += 2 * 128 * n * n_chans
     return wide, narrow
 
 
@@ -317,6 +319,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the flush-overhead, grouped-launch, streaming and small-array measurements")
     ap.add_argument("--no-probe", action="store_true", help="skip the tcgen05 issue-rate probe")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default batch schedule")
     ap.add_argument("--prep-sms", type=int, default=-1,
                     help="SMs building the next launch's operand beside the X-engine (-1 library default, 0 none)")
     args = ap.parse_args()
@@ -353,6 +356,11 @@ def main():
     torch.cuda.synchronize()
     xc = corr.Correlator(N_IN, N_CHAN, T_BLOCK, N_POL, path=args.path)
     xc.set_prep_sms(args.prep_sms)
+    tuning = None
+    if args.path == "fp8tc" and not args.no_autotune and args.prep_sms == -1:
+        # the batch schedule (tile plan, blocks per launch, concurrent build SMs) timed on these blocks
+        tuning = xc.autotune(blocks, reps=2)
+    xc_plan = xc.tile_plan if args.path.startswith("fp8tc") else 0
     cross_out = torch.empty(xc.out_shape(corr.CORR_WHAT_CROSS), dtype=torch.int64, device=dev)
     autos_out = torch.empty(xc.out_shape(corr.CORR_WHAT_AUTO), dtype=torch.int64, device=dev)
 
@@ -441,7 +449,7 @@ def main():
     if args.path.startswith("fp8tc") and probe:
         # the same kernel against the tcgen05 issue rate measured on this GPU just before the timed
         # region: the ideal launch time of the MMAs the tile plan issues, and the useful rate's share
-        wide, narrow = issued_flops_per_sample(N_IN, N_CHAN)
+        wide, narrow = issued_flops_per_sample(N_IN, N_CHAN, xc_plan)
         samples = T_BLOCK * blocks_per_launch
         ideal_ms = (wide * samples / (probe["tflops_n256"] * 1e12) + narrow * samples / (probe["tflops_n128"] * 1e12)) * 1e3
         roof["issue_probe"] = dict(probe)
@@ -545,7 +553,8 @@ def main():
             "vs_baseline": None, "dtype": {"i8mma": "s8", "fp32": "f32"}.get(args.path, "e4m3"), "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_inputs": N_IN, "n_chans": N_CHAN, "n_time_per_block": T_BLOCK,
                        "blocks_per_step": N_BLOCKS, "n_pol": N_POL, "path": args.path,
-                       "prep_sms": prep_sms,
+                       "prep_sms": prep_sms, "tile_plan": xc_plan,
+                       "blocks_per_launch": blocks_per_launch, "autotune": tuning,
                        "l2": "inputs 8 GiB > L2, no flush needed",
                        "parallelism": "channel shards: each GPU a contiguous 128-channel range of a 128 x n_gpus-channel band",
                        "band_channels": N_CHAN * world},

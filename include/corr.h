@@ -148,6 +148,42 @@ int corr_set_prep_sms(corr_ctx* ctx, int sms);
 int corr_get_prep_sms(const corr_ctx* ctx);
 
 /*
+ * corr_set_batch_blocks - blocks of n_time_per_block samples that corr_accumulate_batch multiplies per
+ * tensor-core launch of the two-pass tensor path (each launch reads and writes the int64 accumulators
+ * once, Sec. 2.5's integration of groups of spectra; longer launches cost less per sample until the
+ * operand the SMs share no longer fits in L2). 0 restores the default (corr_batch_blocks). Resizes the
+ * operand buffers (K blocks each) after waiting for the device; CORR_ERR_OOM leaves the previous
+ * size. CORR_ERR_ARG above the shape's cap (8 GiB of operand). corr_get_batch_blocks returns the value
+ * in use. Results are identical for every value.
+ */
+int corr_set_batch_blocks(corr_ctx* ctx, int blocks);
+int corr_get_batch_blocks(const corr_ctx* ctx);
+
+/* Schedule chosen by corr_autotune. */
+typedef struct corr_tuning {
+  int tile_plan;       /* corr_set_tile_plan */
+  int batch_blocks;    /* corr_set_batch_blocks */
+  int prep_sms;        /* corr_set_prep_sms */
+  int n_tried;         /* schedules timed (0: taken from the cache) */
+  double ms_per_block; /* the chosen schedule's time per block */
+} corr_tuning;
+
+/*
+ * corr_autotune - times the two-pass tensor path's schedules on the caller's own n_blocks device
+ * blocks (uint8[T][C][N] each; the batch of corr_accumulate_batch) and keeps the fastest for this
+ * context: tile plan 0, 1 or 2 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
+ * the operand cap) x SMs of a concurrent operand build (0, a quarter of the SMs, all of them; only for
+ * batches of several launches on shapes the build takes). Each schedule runs the batch once to warm up
+ * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream. The results are cached in-process
+ * by (N, C, T, n_pol, SMs, n_blocks), and in the file named by CORR_AUTOTUNE_CACHE if set; a cached
+ * choice is applied without timing. Afterwards the accumulators and sample counts are zero (the trials
+ * added into them). Synchronizes the device. out (optional) receives the choice. No counterpart in the
+ * paper. CORR_ERR_STATE unless the context runs the two-pass tensor path.
+ */
+int corr_autotune(corr_ctx* ctx, const void* const* d_blocks, int n_blocks, int reps, corr_tuning* out,
+                  void* cuda_stream);
+
+/*
  * corr_set_flush_period - maximum number of samples accumulated in on-chip FP32/int32 partial sums
  * before they are added to the int64 accumulators (the paper integrates 8000-spectrum groups and
  * then sums 27 of them, Sec. 2.5; the flush cadence is this library's choice). 0 restores the

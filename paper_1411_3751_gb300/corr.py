@@ -34,6 +34,9 @@ SIGNATURES = [
     ("corr_tile_plan", _c_int, [_c_int, _c_int, _c_vp, _c_int]),
     ("corr_set_prep_sms", _c_int, [_c_vp, _c_int]),
     ("corr_get_prep_sms", _c_int, [_c_vp]),
+    ("corr_set_batch_blocks", _c_int, [_c_vp, _c_int]),
+    ("corr_get_batch_blocks", _c_int, [_c_vp]),
+    ("corr_autotune", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_int, _c_vp, _c_vp]),
     ("corr_set_flush_period", _c_int, [_c_vp, _c_int]),
     ("corr_accumulate", _c_int, [_c_vp, _c_vp, _c_vp]),
     ("corr_accumulate_batch", _c_int, [_c_vp, ctypes.POINTER(ctypes.c_void_p), _c_int, _c_vp]),
@@ -142,6 +145,28 @@ def corr_set_prep_sms(ctx: int, sms: int) -> int:
 
 def corr_get_prep_sms(ctx: int) -> int:
     return _check(_lib.corr_get_prep_sms(ctx), "corr_get_prep_sms")
+
+
+def corr_set_batch_blocks(ctx: int, blocks: int) -> int:
+    return _check(_lib.corr_set_batch_blocks(ctx, blocks), "corr_set_batch_blocks")
+
+
+def corr_get_batch_blocks(ctx: int) -> int:
+    return _check(_lib.corr_get_batch_blocks(ctx), "corr_get_batch_blocks")
+
+
+class CorrTuning(ctypes.Structure):
+    _fields_ = [("tile_plan", ctypes.c_int), ("batch_blocks", ctypes.c_int), ("prep_sms", ctypes.c_int),
+                ("n_tried", ctypes.c_int), ("ms_per_block", ctypes.c_double)]
+
+
+def corr_autotune(ctx: int, d_blocks, reps: int, stream: int) -> dict:
+    """Time the batch schedules on the given device blocks, keep the fastest; returns the choice."""
+    arr = (ctypes.c_void_p * len(d_blocks))(*[int(p) for p in d_blocks])
+    t = CorrTuning()
+    _check(_lib.corr_autotune(ctx, arr, len(d_blocks), reps, ctypes.byref(t), stream), "corr_autotune")
+    return {"tile_plan": t.tile_plan, "batch_blocks": t.batch_blocks, "prep_sms": t.prep_sms, "n_tried": t.n_tried,
+            "ms_per_block": t.ms_per_block}
 
 
 def corr_set_flush_period(ctx: int, n_samples: int) -> int:
@@ -426,6 +451,20 @@ class Correlator:
     @property
     def prep_sms(self) -> int:
         return corr_get_prep_sms(self.ctx)
+
+    def set_batch_blocks(self, blocks: int):
+        """Blocks per tensor-core launch of batches (0: the default)."""
+        corr_set_batch_blocks(self.ctx, blocks)
+
+    @property
+    def batch_blocks(self) -> int:
+        return corr_get_batch_blocks(self.ctx)
+
+    def autotune(self, blocks, reps: int = 2, stream=None) -> dict:
+        """Time the batch schedules on these device blocks and keep the fastest (accumulators end at zero)."""
+        for b in blocks:
+            self._check_samples(b, True)
+        return corr_autotune(self.ctx, [b.data_ptr() for b in blocks], reps, _stream_handle(stream))
 
     def set_tile_plan(self, plan: int):
         """Work-item plan of the two-pass tensor path (0 default, 1, 2: c-block pairs)."""

@@ -389,6 +389,34 @@ int ensure_operand_scratch(corr_ctx* c) {
   return CORR_OK;
 }
 
+int max_batch_blocks(const corr_ctx* c) {
+  const unsigned long long ob = c->L.op_bytes > 0 ? c->L.op_bytes : 1;
+  const unsigned long long k = kMaxOperandBuffer / ob;
+  return k < 1 ? 1 : (k > 64 ? 64 : (int)k);
+}
+
+int set_batch_blocks(corr_ctx* c, int K) {
+  if (K == c->L.K_batch) return CORR_OK;
+  const cudaError_t e = cudaDeviceSynchronize();  // queued launches read the current buffers
+  if (e != cudaSuccess) return cuda_fail(e, "set_batch_blocks: synchronize");
+  const bool had_op = c->d_op != nullptr;
+  const int old_K = c->L.K_batch;
+  cudaFree(c->d_op);
+  cudaFree(c->d_op2);
+  c->d_op = nullptr;
+  c->d_op2 = nullptr;
+  c->L.K_batch = K;
+  c->L.op_buf_bytes = c->L.op_bytes * (size_t)K;
+  if (!had_op) return CORR_OK;
+  const int rc = ensure_operand_scratch(c);
+  if (rc == CORR_OK) return CORR_OK;
+  const std::string msg = g_err;
+  c->L.K_batch = old_K;  // back to the old size, which fitted before
+  c->L.op_buf_bytes = c->L.op_bytes * (size_t)old_K;
+  ensure_operand_scratch(c);
+  return fail(rc, msg);
+}
+
 // SMs that build the next chunk's operand while the X-engine multiplies the current one.
 int prep_sms_for(const corr_ctx* c) {
   if (c->prep_sms >= 0) return c->prep_sms;
@@ -577,6 +605,7 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
   c->L = L;
   c->path = CORR_PATH_AUTO;
   c->prep_sms = -1;
+  c->K_default = L.K_batch;
   c->device = dev;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (c->num_sms < 1) c->num_sms = 1;
@@ -665,6 +694,150 @@ int corr_set_prep_sms(corr_ctx* c, int sms) {
 }
 
 int corr_get_prep_sms(const corr_ctx* c) { return c ? prep_sms_for(c) : CORR_ERR_ARG; }
+
+int corr_set_batch_blocks(corr_ctx* c, int blocks) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_set_batch_blocks: NULL context");
+  const int kmax = max_batch_blocks(c);
+  if (blocks < 0 || blocks > kmax)
+    return fail(CORR_ERR_ARG, "corr_set_batch_blocks: need 0 (the default) .. " + std::to_string(kmax) +
+                                  " (an 8 GiB operand buffer) for this shape");
+  return set_batch_blocks(c, blocks == 0 ? c->K_default : blocks);
+}
+
+int corr_get_batch_blocks(const corr_ctx* c) { return c ? c->L.K_batch : CORR_ERR_ARG; }
+
+namespace {
+std::mutex g_ctx_tune_mu;
+// (N, C, T, n_pol, SMs, blocks) -> (plan, blocks per launch, build SMs, ms per block)
+std::map<std::tuple<int, int, int, int, int, int>, std::tuple<int, int, int, double>> g_ctx_tune;
+bool g_ctx_tune_loaded = false;
+
+void ctx_tune_load() {
+  if (g_ctx_tune_loaded) return;
+  g_ctx_tune_loaded = true;
+  const char* path = std::getenv("CORR_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return;
+  char tag[16];
+  int a, b, cc, d, e, f, p, k, q;
+  double ms;
+  while (std::fscanf(fh, "%15s", tag) == 1) {
+    if (std::strcmp(tag, "batch") == 0 &&
+        std::fscanf(fh, "%d %d %d %d %d %d %d %d %d %lf", &a, &b, &cc, &d, &e, &f, &p, &k, &q, &ms) == 10)
+      g_ctx_tune[std::make_tuple(a, b, cc, d, e, f)] = std::make_tuple(p, k, q, ms);
+    else {
+      int ch;  // skip the rest of a line of another kind
+      while ((ch = std::fgetc(fh)) != EOF && ch != '\n') {
+      }
+    }
+  }
+  std::fclose(fh);
+}
+
+void ctx_tune_store(const std::tuple<int, int, int, int, int, int>& key, const std::tuple<int, int, int, double>& v) {
+  g_ctx_tune[key] = v;
+  const char* path = std::getenv("CORR_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "batch %d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(key), std::get<1>(key), std::get<2>(key),
+               std::get<3>(key), std::get<4>(key), std::get<5>(key), std::get<0>(v), std::get<1>(v), std::get<2>(v),
+               std::get<3>(v));
+  std::fclose(fh);
+}
+}  // namespace
+
+int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int reps, corr_tuning* out, void* stream) {
+  if (!c) return fail(CORR_ERR_ARG, "corr_autotune: NULL context");
+  if (n_blocks < 1 || !d_blocks || reps < 1 || reps > 100)
+    return fail(CORR_ERR_ARG, "corr_autotune: need n_blocks >= 1 blocks and 1 <= reps <= 100");
+  for (int b = 0; b < n_blocks; ++b)
+    if (!d_blocks[b]) return fail(CORR_ERR_ARG, "corr_autotune: NULL block " + std::to_string(b));
+  if (resolved_path(c) != CORR_PATH_FP8TC)
+    return fail(CORR_ERR_STATE, "corr_autotune: tunes the two-pass tensor path (CORR_PATH_FP8TC / AUTO)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint8_t* const* blocks = reinterpret_cast<const uint8_t* const*>(d_blocks);
+  std::lock_guard<std::mutex> lock(g_ctx_tune_mu);
+  ctx_tune_load();
+  const auto key = std::make_tuple(c->L.s.N, c->L.s.C, c->L.s.T, c->L.s.npol, c->num_sms, n_blocks);
+  int best_plan = c->tile_plan, best_K = c->L.K_batch, best_prep = prep_sms_for(c), tried = 0;
+  double best_ms = 0.0;
+  int rc = CORR_OK;
+  const auto hit = g_ctx_tune.find(key);
+  if (hit != g_ctx_tune.end()) {
+    std::tie(best_plan, best_K, best_prep, best_ms) = hit->second;
+  } else {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "corr_autotune: events");
+    bool tma_ok = true;
+    for (int b = 0; b < n_blocks; ++b) tma_ok = tma_ok && f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
+    std::vector<int> Ks = {1, 2, 4, 8, c->K_default};
+    std::sort(Ks.begin(), Ks.end());
+    Ks.erase(std::unique(Ks.begin(), Ks.end()), Ks.end());
+    best_ms = 1e300;
+    for (int plan = 0; plan <= 2 && rc == CORR_OK; ++plan) {
+      rc = set_tile_plan(c, plan);
+      for (int K : Ks) {
+        if (rc != CORR_OK) break;
+        if (K > max_batch_blocks(c) || (K > n_blocks && K != c->K_default)) continue;
+        const std::vector<int> preps = (tma_ok && plan != 2 && n_blocks > K)
+                                           ? std::vector<int>{0, c->num_sms / 4, c->num_sms}
+                                           : std::vector<int>{0};
+        for (int prep : preps) {
+          if ((rc = set_batch_blocks(c, K)) != CORR_OK) {
+            if (rc == CORR_ERR_OOM) rc = CORR_OK;  // this launch length does not fit: skip it
+            break;
+          }
+          c->prep_sms = prep;
+          float ms = 0.f;
+          for (int rep = 0; rep <= reps && rc == CORR_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, st);
+            rc = accumulate_batch_chunks(c, blocks, n_blocks, st);
+          }
+          if (rc != CORR_OK) break;
+          cudaEventRecord(e1, st);
+          const cudaError_t e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) {
+            rc = cuda_fail(e, "corr_autotune: timing");
+            break;
+          }
+          cudaEventElapsedTime(&ms, e0, e1);
+          const double per_block = (double)ms / reps / n_blocks;
+          ++tried;
+          if (per_block < best_ms) {
+            best_ms = per_block;
+            best_plan = plan;
+            best_K = K;
+            best_prep = prep;
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == CORR_OK) ctx_tune_store(key, std::make_tuple(best_plan, best_K, best_prep, best_ms));
+  }
+  if (rc == CORR_OK) rc = set_tile_plan(c, best_plan);
+  if (rc == CORR_OK) rc = set_batch_blocks(c, best_K);
+  c->prep_sms = best_prep;
+  // the trials added into the accumulators: start from zero
+  if (rc == CORR_OK) rc = corr_reset(c, CORR_WHAT_CROSS | CORR_WHAT_AUTO, stream);
+  if (rc == CORR_OK) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "corr_autotune: synchronize");
+  }
+  if (rc != CORR_OK) return rc;
+  if (out) {
+    out->tile_plan = best_plan;
+    out->batch_blocks = best_K;
+    out->prep_sms = best_prep;
+    out->n_tried = tried;
+    out->ms_per_block = best_ms;
+  }
+  return CORR_OK;
+}
 
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles) {
   if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 2 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))

@@ -55,6 +55,7 @@ struct corr_ctx {
   // overlapped batches: the operand of chunk j + 1 is built on prep_sms SMs (TMA build kernel, on
   // prep_stream) while the X-engine multiplies chunk j on the others; d_op2 is the second buffer
   int prep_sms;           // -1: automatic, 0: no overlap
+  int K_default;          // blocks per batch launch chosen by the L2 rule (corr_set_batch_blocks 0)
   uint8_t* d_op2;
   CUtensorMap tmap2;
   cudaStream_t prep_stream;
@@ -95,6 +96,12 @@ bool timer_begin(corr_ctx* c, int k, cudaStream_t st);
 void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun);
 // tile list and channel-major work list of the tensor paths for plan 0, 1 or 2
 int set_tile_plan(corr_ctx* c, int plan);
+// blocks per tensor-core launch of batches (reallocates the operand buffers once the device is idle)
+int set_batch_blocks(corr_ctx* c, int K);
+// largest blocks per launch the operand buffer cap allows for this shape
+int max_batch_blocks(const corr_ctx* c);
+// n device blocks through the two-pass tensor path (batch schedule of the context's settings)
+int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st);
 // T_blk samples of a device block [T_blk][C][N] through the context's current path
 int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t st);
 

@@ -46,8 +46,11 @@ void tune_load() {
   if (!path) return;
   FILE* fh = std::fopen(path, "r");
   if (!fh) return;
+  // lines "N C T n_pol SMs plan" (other lines in the file belong to other tuners)
+  char line[256];
   int a, b, c, d, e, p;
-  while (std::fscanf(fh, "%d %d %d %d %d %d", &a, &b, &c, &d, &e, &p) == 6) g_tune[std::make_tuple(a, b, c, d, e)] = p;
+  while (std::fgets(line, sizeof line, fh))
+    if (std::sscanf(line, "%d %d %d %d %d %d", &a, &b, &c, &d, &e, &p) == 6) g_tune[std::make_tuple(a, b, c, d, e)] = p;
   std::fclose(fh);
 }
 

@@ -51,16 +51,18 @@ def source_hash(kernel_files):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_files, profile_md, blocks_per_launch):
+def profiled_traffic(kernel_files, profile_md, blocks_per_launch, tile_plan=None):
     """DRAM bytes per launch recorded by an ncu capture (profiles/), if the kernel sources still match
-    and the capture covered launches of the same size."""
+    and the capture covered launches of the same size (and tile plan, where it records one)."""
     try:
         text = open(os.path.join(ROOT, "profiles", profile_md)).read()
-        keys = ("traffic_bytes_per_launch:", "source_sha256:", "blocks_per_launch:")
+        keys = ("traffic_bytes_per_launch:", "source_sha256:", "blocks_per_launch:", "tile_plan:")
         vals = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(keys))
         if vals.get("source_sha256", "").strip() != source_hash(kernel_files):
             return None
         if abs(float(vals.get("blocks_per_launch", "1")) - blocks_per_launch) > 1e-9:
+            return None
+        if tile_plan is not None and "tile_plan" in vals and int(vals["tile_plan"]) != tile_plan:
             return None
         return int(vals["traffic_bytes_per_launch"])
     except Exception:
@@ -71,7 +73,7 @@ XENG_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"]
 PREP_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh"]
 
 
-def step_traffic(xeng_launches, prep_launches, blocks_per_launch):
+def step_traffic(xeng_launches, prep_launches, blocks_per_launch, tile_plan):
     """DRAM bytes of one step from the ncu captures summarised in profiles/ (per launch, source-hash
     checked) against the algorithmic bytes of the step: the input read once, the int64 cross
     accumulators read and written once per X-engine launch, and the dumped visibilities written once."""
@@ -80,7 +82,7 @@ def step_traffic(xeng_launches, prep_launches, blocks_per_launch):
     acc = N_CHAN * corr.corr_n_baselines(N_IN, N_POL) * N_POL * N_POL * 2 * 8
     inp = T_BLOCK * N_BLOCKS * N_CHAN * N_IN
     alg = inp + xeng_launches * 2 * acc + acc
-    x = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch)
+    x = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch, tile_plan)
     pr = profiled_traffic(PREP_SOURCES, "f8_prep_512in_128ch_8192.md", 1)
     out = {"algorithmic_bytes": alg, "xeng_bytes_per_launch": x, "prep_bytes_per_launch": pr,
            "xeng_launches": xeng_launches, "prep_launches": prep_launches}
@@ -438,7 +440,7 @@ def main():
         sm_share = 1.0
     traffic = None
     if args.path == "fp8tc":
-        traffic = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch)
+        traffic = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch, xc_plan)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel",
                                            "i8mma": "xeng_i8mma_kernel"}.get(args.path, "xeng_fp32_kernel"),
@@ -457,7 +459,7 @@ def main():
         roof["frac_issue"] = ideal_ms / per_launch_ms
         roof["frac_useful_of_issue_peak"] = achieved / probe["tflops_n256"]
     if args.path == "fp8tc":
-        roof["step_traffic"] = step_traffic(xeng_n / args.steps, unpack_n / args.steps, blocks_per_launch)
+        roof["step_traffic"] = step_traffic(xeng_n / args.steps, unpack_n / args.steps, blocks_per_launch, xc_plan)
 
     # end-to-end through the public API from pinned host buffers
     e2e = None

@@ -174,7 +174,8 @@ typedef struct corr_tuning {
  * context: tile plan 0, 1 or 2 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
  * the operand cap) x SMs of a concurrent operand build (0, a quarter of the SMs, all of them; only for
  * batches of several launches on shapes the build takes). Each schedule runs the batch once to warm up
- * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream. The results are cached in-process
+ * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream; the default schedule is timed
+ * first and another replaces the best only when at least 1% faster. The results are cached in-process
  * by (N, C, T, n_pol, SMs, n_blocks), and in the file named by CORR_AUTOTUNE_CACHE if set; a cached
  * choice is applied without timing. Afterwards the accumulators and sample counts are zero (the trials
  * added into them). Synchronizes the device. out (optional) receives the choice. No counterpart in the

@@ -773,46 +773,53 @@ int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int re
       return cuda_fail(cudaGetLastError(), "corr_autotune: events");
     bool tma_ok = true;
     for (int b = 0; b < n_blocks; ++b) tma_ok = tma_ok && f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
+    // candidates: the default schedule (plan 0, the default launch length, sequential) first; another
+    // replaces the best so far only when it is at least 1% faster, so near-ties keep the default
+    std::vector<std::tuple<int, int, int>> cand;
+    cand.emplace_back(0, c->K_default, 0);
     std::vector<int> Ks = {1, 2, 4, 8, c->K_default};
     std::sort(Ks.begin(), Ks.end());
     Ks.erase(std::unique(Ks.begin(), Ks.end()), Ks.end());
-    best_ms = 1e300;
-    for (int plan = 0; plan <= 2 && rc == CORR_OK; ++plan) {
-      rc = set_tile_plan(c, plan);
+    for (int plan = 0; plan <= 2; ++plan)
       for (int K : Ks) {
-        if (rc != CORR_OK) break;
         if (K > max_batch_blocks(c) || (K > n_blocks && K != c->K_default)) continue;
         const std::vector<int> preps = (tma_ok && plan != 2 && n_blocks > K)
                                            ? std::vector<int>{0, c->num_sms / 4, c->num_sms}
                                            : std::vector<int>{0};
-        for (int prep : preps) {
-          if ((rc = set_batch_blocks(c, K)) != CORR_OK) {
-            if (rc == CORR_ERR_OOM) rc = CORR_OK;  // this launch length does not fit: skip it
-            break;
-          }
-          c->prep_sms = prep;
-          float ms = 0.f;
-          for (int rep = 0; rep <= reps && rc == CORR_OK; ++rep) {
-            if (rep == 1) cudaEventRecord(e0, st);
-            rc = accumulate_batch_chunks(c, blocks, n_blocks, st);
-          }
-          if (rc != CORR_OK) break;
-          cudaEventRecord(e1, st);
-          const cudaError_t e = cudaEventSynchronize(e1);
-          if (e != cudaSuccess) {
-            rc = cuda_fail(e, "corr_autotune: timing");
-            break;
-          }
-          cudaEventElapsedTime(&ms, e0, e1);
-          const double per_block = (double)ms / reps / n_blocks;
-          ++tried;
-          if (per_block < best_ms) {
-            best_ms = per_block;
-            best_plan = plan;
-            best_K = K;
-            best_prep = prep;
-          }
-        }
+        for (int prep : preps)
+          if (!(plan == 0 && K == c->K_default && prep == 0)) cand.emplace_back(plan, K, prep);
+      }
+    best_ms = 1e300;
+    for (const auto& cd : cand) {
+      if (rc != CORR_OK) break;
+      const int plan = std::get<0>(cd), K = std::get<1>(cd), prep = std::get<2>(cd);
+      if (c->tile_plan != plan && (rc = set_tile_plan(c, plan)) != CORR_OK) break;
+      if ((rc = set_batch_blocks(c, K)) != CORR_OK) {
+        if (rc != CORR_ERR_OOM) break;
+        rc = CORR_OK;  // this launch length does not fit: skip it
+        continue;
+      }
+      c->prep_sms = prep;
+      float ms = 0.f;
+      for (int rep = 0; rep <= reps && rc == CORR_OK; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, st);
+        rc = accumulate_batch_chunks(c, blocks, n_blocks, st);
+      }
+      if (rc != CORR_OK) break;
+      cudaEventRecord(e1, st);
+      const cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "corr_autotune: timing");
+        break;
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per_block = (double)ms / reps / n_blocks;
+      ++tried;
+      if (per_block < 0.99 * best_ms) {
+        best_ms = per_block;
+        best_plan = plan;
+        best_K = K;
+        best_prep = prep;
       }
     }
     cudaEventDestroy(e0);

@@ -110,11 +110,10 @@ int corr_get_path(const corr_ctx* ctx);
  * (Sec. 2.5's pairwise products) into work items: 0 (default) tiles of 64 c-inputs x 128 a-inputs
  * (64 on the diagonal); 1 tiles of 64 x 64; 2 pairs of 64-input c-blocks against 128 a-inputs, the
  * two halves sharing one operand tile (a third fewer operand bytes per product; the pair fills both
- * TMEM accumulators, so its drain is not overlapped with the next item); 3 the items of plan 2 fed
- * through a ring of twice as many stages of half the samples. Results are identical for every plan.
- * Waits for the device (queued launches read the current work list). CORR_ERR_ARG for another value.
- * Group launches (corr_group_*) always use plan 0 or 1. corr_get_tile_plan returns the current plan
- * (CORR_ERR_ARG for a NULL context).
+ * TMEM accumulators, so its drain is not overlapped with the next item). Results are identical for
+ * every plan. Waits for the device (queued launches read the current work list). CORR_ERR_ARG for
+ * another value. Group launches (corr_group_*) always use plan 0 or 1. corr_get_tile_plan returns
+ * the current plan (CORR_ERR_ARG for a NULL context).
  */
 int corr_set_tile_plan(corr_ctx* ctx, int plan);
 int corr_get_tile_plan(const corr_ctx* ctx);
@@ -126,7 +125,7 @@ int corr_get_tile_plan(const corr_ctx* ctx);
  * - 1 (nb operand rows, two per input). For plan 2, extra = nb1 | (hi << 16) describes its second half:
  * c-inputs c0 + 64 .. c0 + 127 against nb1 / 2 a-inputs from a0 + 64 hi; otherwise extra = 0.
  * Together the tiles cover every pair a >= c of the triangle exactly once (inputs >= n_inputs are
- * padding). Plan 3 has plan 2's tiles. CORR_ERR_ARG for n_inputs outside 1 .. 2^20, plan outside 0 .. 3, or max_tiles > 0 with
+ * padding). CORR_ERR_ARG for n_inputs outside 1 .. 2^20, plan outside 0 .. 2, or max_tiles > 0 with
  * a NULL buffer.
  */
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
@@ -172,7 +171,7 @@ typedef struct corr_tuning {
 /*
  * corr_autotune - times the two-pass tensor path's schedules on the caller's own n_blocks device
  * blocks (uint8[T][C][N] each; the batch of corr_accumulate_batch) and keeps the fastest for this
- * context: tile plan 0, 1, 2 or 3 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
+ * context: tile plan 0, 1 or 2 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
  * the operand cap) x SMs of a concurrent operand build (0, a quarter of the SMs, all of them; only for
  * batches of several launches on shapes the build takes). Each schedule runs the batch once to warm up
  * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream; the default schedule is timed

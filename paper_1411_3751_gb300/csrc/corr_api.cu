@@ -316,13 +316,12 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
 
 
 // Tile plan of the tensor paths: the tile list (fused path) and the channel-major work list
-// (two-pass path) for plan 0, 1, 2 or 3 (see f8_tile_plan).
+// (two-pass path) for plan 0, 1 or 2 (see f8_tile_plan).
 
 int set_tile_plan(corr_ctx* c, int plan) {
   // the fused path has no wide mode: it keeps plan 0 under plan 2
-  const bool wide = plan == 2 || plan == 3;
-  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, wide ? 0 : plan);
-  const std::vector<F8Tile> tw = wide ? f8_tile_plan(c->L.s.N, c->L.R, plan) : t8;
+  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan == 2 ? 0 : plan);
+  const std::vector<F8Tile> tw = plan == 2 ? f8_tile_plan(c->L.s.N, c->L.R, 2) : t8;
   std::vector<WorkItem> items;
   items.reserve((size_t)c->L.s.C * tw.size());
   for (int f = 0; f < c->L.s.C; ++f)
@@ -357,7 +356,6 @@ XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flu
   XengArgs a;
   std::memset(&a, 0, sizeof(a));
   a.a[0].tmap = map;
-  a.a[0].tmap_short = c->tmap_short;  // the wide plans run on the first operand buffer only
   a.a[0].cross = c->d_cross;
   a.a[0].autos = c->d_autos;
   a.a[0].Bs = c->L.s.Bs;
@@ -368,8 +366,7 @@ XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flu
   a.T_run = T_run;
   a.flush_len = flush;
   a.err = c->d_err;
-  a.wide = (c->tile_plan == 2 || c->tile_plan == 3) ? 1 : 0;
-  a.short_stages = c->tile_plan == 3 ? 1 : 0;
+  a.wide = c->tile_plan == 2 ? 1 : 0;
   return a;
 }
 
@@ -384,9 +381,7 @@ int ensure_operand_scratch(corr_ctx* c) {
   cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_buf_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
   std::string err;
-  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0 ||
-      encode_op_tensor_map(&c->tmap_short, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err,
-                           kF8Kt / 2) != 0) {
+  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
     cudaFree(c->d_op);
     c->d_op = nullptr;
     return fail(CORR_ERR_CUDA, err);
@@ -519,7 +514,7 @@ int accumulate_batch_overlap(corr_ctx* c, const uint8_t* const* blocks, int n, c
 int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
   // overlapped schedule when there are at least two chunks and the TMA build takes the shape
   const int k = prep_sms_for(c);
-  if (k > 0 && k <= c->num_sms && n > c->L.K_batch && c->tile_plan < 2) {
+  if (k > 0 && k <= c->num_sms && n > c->L.K_batch && c->tile_plan != 2) {
     bool ok = true;
     for (int b = 0; b < n && ok; ++b) ok = f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
     if (ok) {
@@ -681,7 +676,7 @@ int corr_get_path(const corr_ctx* c) { return c ? resolved_path(c) : CORR_ERR_AR
 
 int corr_set_tile_plan(corr_ctx* c, int plan) {
   if (!c) return fail(CORR_ERR_ARG, "corr_set_tile_plan: NULL context");
-  if (plan < 0 || plan > 3) return fail(CORR_ERR_ARG, "corr_set_tile_plan: plan must be 0, 1, 2 or 3");
+  if (plan < 0 || plan > 2) return fail(CORR_ERR_ARG, "corr_set_tile_plan: plan must be 0, 1 or 2");
   // the work lists are read by queued launches: replace them once those are done
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "corr_set_tile_plan: synchronize");
@@ -785,10 +780,10 @@ int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int re
     std::vector<int> Ks = {1, 2, 4, 8, c->K_default};
     std::sort(Ks.begin(), Ks.end());
     Ks.erase(std::unique(Ks.begin(), Ks.end()), Ks.end());
-    for (int plan = 0; plan <= 3; ++plan)
+    for (int plan = 0; plan <= 2; ++plan)
       for (int K : Ks) {
         if (K > max_batch_blocks(c) || (K > n_blocks && K != c->K_default)) continue;
-        const std::vector<int> preps = (tma_ok && plan < 2 && n_blocks > K)
+        const std::vector<int> preps = (tma_ok && plan != 2 && n_blocks > K)
                                            ? std::vector<int>{0, c->num_sms / 4, c->num_sms}
                                            : std::vector<int>{0};
         for (int prep : preps)
@@ -852,8 +847,8 @@ int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int re
 }
 
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles) {
-  if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 3 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))
-    return fail(CORR_ERR_ARG, "corr_tile_plan: need 1 <= n_inputs <= 2^20, plan 0..3, a buffer for max_tiles > 0");
+  if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 2 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))
+    return fail(CORR_ERR_ARG, "corr_tile_plan: need 1 <= n_inputs <= 2^20, plan 0..2, a buffer for max_tiles > 0");
   const int R = (int)round_up(2LL * n_inputs, kF8RowAlign);
   const std::vector<F8Tile> t = f8_tile_plan(n_inputs, R, plan);
   if (t.size() > (size_t)0x7fffffff) return fail(CORR_ERR_ARG, "corr_tile_plan: too many tiles");

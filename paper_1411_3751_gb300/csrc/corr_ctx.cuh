@@ -52,7 +52,6 @@ struct corr_ctx {
   int* d_err;
   uint8_t* d_op;          // operand scratch of the two-pass tensor path (K_batch blocks)
   CUtensorMap tmap;
-  CUtensorMap tmap_short;  // the same buffer with boxes of half the samples (tile plan 3)
   // overlapped batches: the operand of chunk j + 1 is built on prep_sms SMs (TMA build kernel, on
   // prep_stream) while the X-engine multiplies chunk j on the others; d_op2 is the second buffer
   int prep_sms;           // -1: automatic, 0: no overlap
@@ -95,7 +94,7 @@ int flush_for(const corr_ctx* c, int path);
 // opt-in kernel timing around a launch on st (no-ops unless profiling is on)
 bool timer_begin(corr_ctx* c, int k, cudaStream_t st);
 void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun);
-// tile list and channel-major work list of the tensor paths for plan 0, 1, 2 or 3
+// tile list and channel-major work list of the tensor paths for plan 0, 1 or 2
 int set_tile_plan(corr_ctx* c, int plan);
 // blocks per tensor-core launch of batches (reallocates the operand buffers once the device is idle)
 int set_batch_blocks(corr_ctx* c, int K);

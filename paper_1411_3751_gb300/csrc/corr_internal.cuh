@@ -60,8 +60,7 @@ struct WorkItem {
 // different N correlated in one persistent launch).
 constexpr int kMaxGroupArrays = 8;
 struct XengArray {
-  CUtensorMap tmap;        // operand op[C][T_span][R], boxes of 128 rows x kF8Kt samples
-  CUtensorMap tmap_short;  // the same operand, boxes of 128 rows x kF8Kt / 2 samples (tile plan 3)
+  CUtensorMap tmap;  // operand op[C][T_span][R]
   long long* cross;
   long long* autos;
   long long Bs;
@@ -74,8 +73,7 @@ struct XengArgs {
   int T_run;      // samples multiplied per item (multiple of kF8Kt)
   int flush_len;  // samples per in-chip partial sum
   int* err;
-  int wide;          // items are c-block pairs of tile plans 2 and 3 (see f8_tile_plan)
-  int short_stages;  // ring stages of kF8Kt / 2 samples (tile plan 3)
+  int wide;       // items are c-block pairs of tile plan 2 (see f8_tile_plan)
 };
 
 constexpr int kF8Kt = 128;             // time samples per pipeline stage
@@ -141,10 +139,10 @@ cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st);
 
 // Tile plans of the triangle (a >= c) for N inputs with R operand rows: plan 0 = a-side spans of
 // 128 inputs (N = 256 rows) with a half-width first span on odd c-blocks; plan 1 = spans of 64
-// inputs (N = 128) everywhere; plans 2 and 3 = pairs of c-blocks (c0, c0 + 64) against a-spans of
-// 128 inputs, both halves sharing the B operand (wide mode of the two-pass X-engine; plan 3 runs it
-// with ring stages of half the samples): nb = half 0's width, pad = half 1's width | (1 << 16 when
-// half 1 starts at the second B atom, on a diagonal pair); half 1's width is 0 when c0 + 64 >= N.
+// inputs (N = 128) everywhere; plan 2 = pairs of c-blocks (c0, c0 + 64) against a-spans of 128
+// inputs, both halves sharing the B operand (wide mode of the two-pass X-engine): nb = half 0's
+// width, pad = half 1's width | (1 << 16 when half 1 starts at the second B atom, on a diagonal
+// pair); half 1's width is 0 when c0 + 64 >= N.
 std::vector<F8Tile> f8_tile_plan(int N, int R, int plan);
 
 size_t f8_smem_bytes();
@@ -181,7 +179,7 @@ cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, 
 void set_last_error(const std::string& msg);
 
 // Tensor-map encoding through the driver entry point (no libcuda link dependency).
-int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err, int box_t = kF8Kt);
+int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err);
 // Raw input in[T][C][N] as a 3-D map, boxes of 64 inputs x 1 channel x 128 samples, no swizzle.
 int encode_input_tensor_map(CUtensorMap* map, const void* d_in, int N, int C, int T, std::string* err);
 

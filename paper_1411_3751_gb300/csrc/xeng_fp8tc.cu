@@ -26,21 +26,13 @@ constexpr int NUM_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int EPI_THREADS = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
-// Ring of the wide mode (tile plans 2 and 3): each item is a pair of 64-input c-blocks against one
-// a-block of up to 128 inputs, both halves sharing the B operand: a stage holds A0 | A1 | B (2 atoms),
-// and the two M = 128 MMAs per K step write TMEM columns 0 .. 255 (half 0) and 256 .. 511 (half 1), so
-// the item uses both accumulators and is drained before the next one starts. Plan 2 uses 3 stages of
-// 128 samples (64 KB), plan 3 6 stages of 64 samples (32 KB), both 192 KB: the same bytes in flight in
-// finer refills.
-template <bool WIDE, int SKT>
-struct XengRing {
-  static constexpr int kSA = 128 * SKT;                    // one 128-row atom of SKT samples
-  static constexpr int kStages = WIDE ? (SKT == 128 ? 3 : 6) : STAGES;
-  static constexpr int kStageBytes = (WIDE ? 2 : 1) * kSA + 2 * kSA;
-  static constexpr int kBOff = (WIDE ? 2 : 1) * kSA;       // B within a stage
-  static_assert(kStages * kStageBytes <= STAGES * STAGE_BYTES, "ring must fit the shared memory of the default");
-  static_assert(kStages <= 2 * STAGES, "barrier slots");
-};
+// Ring of the wide mode (tile plan 2): each item is a pair of 64-input c-blocks against one a-block
+// of up to 128 inputs, both halves sharing the B operand: a stage holds A0 | A1 | B (2 atoms), 64 KB,
+// and the two M = 128 MMAs per K step write TMEM columns 0 .. 255 (half 0) and 256 .. 511 (half 1),
+// so the item uses both accumulators and is drained before the next one starts.
+constexpr int W_STAGES = 3;
+constexpr int W_STAGE_BYTES = 2 * A_BYTES + 2 * B_ATOM;
+static_assert(W_STAGES * W_STAGE_BYTES <= STAGES * STAGE_BYTES, "wide ring must fit the shared memory of the default");
 
 // Operand build + offset sums, one pass over the input (the paper's CPU "unpack" stage, Sec. 2.4,
 // done on the GPU). A unit = 16 inputs (32 operand rows) of one channel; units are numbered across
@@ -163,32 +155,30 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   }
 }
 
-template <bool WIDE, int SKT>
+template <bool WIDE>
 __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_constant__ XengArgs args) {
-  using Ring = XengRing<WIDE, SKT>;
-  constexpr int RING = Ring::kStages;
-  constexpr int RING_BYTES = Ring::kStageBytes;
-  constexpr int B_OFF = Ring::kBOff;  // B within a stage
-  constexpr int SA = Ring::kSA;       // A atom, and each B atom, per stage
+  constexpr int RING = WIDE ? W_STAGES : STAGES;
+  constexpr int RING_BYTES = WIDE ? W_STAGE_BYTES : STAGE_BYTES;
+  constexpr int B_OFF = WIDE ? 2 * A_BYTES : A_BYTES;  // B within a stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + 2 * STAGES;
-  uint64_t* tfull = empty + 2 * STAGES;
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_k = args.T_run / SKT;
-  const int chunk_k = args.flush_len / SKT;
+  const int n_k = args.T_run / KT;
+  const int chunk_k = args.flush_len / KT;
   const long long total = args.n_items;
   const WorkItem* __restrict__ items = args.items;
   int* err = args.err;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < RING; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       ptx::mbar_init(&full[s], 1);
       ptx::mbar_init(&empty[s], 1);
     }
@@ -220,9 +210,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
       for (long long w = blockIdx.x; w < total && !*abort_flag; w += gridDim.x) {
         const WorkItem tl = items[w];
         const int f = tl.f;
-        const CUtensorMap* tmap = SKT == KT ? &args.a[tl.array].tmap : &args.a[tl.array].tmap_short;
+        const CUtensorMap* tmap = &args.a[tl.array].tmap;
         const bool a1 = WIDE && (tl.pad & 0xFFFF) != 0;  // second c-block present
-        const uint32_t bytes = SA * (a1 ? 2 : 1) + (tl.nb == 256 ? 2 * SA : SA);
+        const uint32_t bytes = A_BYTES * (a1 ? 2 : 1) + (tl.nb == 256 ? B_BYTES : B_ATOM);
         for (int ks = 0; ks < n_k; ++ks) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1, WAIT_NS)) {
             record_error(err, abort_flag, 1);
@@ -231,10 +221,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
           uint8_t* a_dst = smem + stage * RING_BYTES;
           uint8_t* b_dst = a_dst + B_OFF;
           ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-          ptx::tma_load_3d(a_dst, tmap, &full[stage], 2 * tl.c0, ks * SKT, f);
-          if (a1) ptx::tma_load_3d(a_dst + SA, tmap, &full[stage], 2 * tl.c0 + 128, ks * SKT, f);
-          ptx::tma_load_3d(b_dst, tmap, &full[stage], 2 * tl.a0, ks * SKT, f);
-          if (tl.nb == 256) ptx::tma_load_3d(b_dst + SA, tmap, &full[stage], 2 * tl.a0 + 128, ks * SKT, f);
+          ptx::tma_load_3d(a_dst, tmap, &full[stage], 2 * tl.c0, ks * KT, f);
+          if (a1) ptx::tma_load_3d(a_dst + A_BYTES, tmap, &full[stage], 2 * tl.c0 + 128, ks * KT, f);
+          ptx::tma_load_3d(b_dst, tmap, &full[stage], 2 * tl.a0, ks * KT, f);
+          if (tl.nb == 256) ptx::tma_load_3d(b_dst + B_ATOM, tmap, &full[stage], 2 * tl.a0 + 128, ks * KT, f);
           issued[stage] = true;
           issued_phase[stage] = phase;
           if (++stage == RING) {
@@ -263,7 +253,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
         // wide mode, half 1: N = nb1 columns of B starting at atom b1 (0, or 1 on a diagonal pair)
         const int nb1 = WIDE ? (tl.pad & 0xFFFF) : 0;
         const uint32_t idesc1 = nb1 == 256 ? id256 : id128;
-        const uint32_t b1_off = WIDE && (tl.pad >> 16) ? (uint32_t)SA : 0u;
+        const uint32_t b1_off = WIDE && (tl.pad >> 16) ? (uint32_t)B_ATOM : 0u;
         for (int k0 = 0; k0 < n_k && ok; k0 += chunk_k) {
           const int k1 = min(k0 + chunk_k, n_k);
           if (!ptx::mbar_wait(&tempty[acc], (use[acc] & 1) ^ 1, WAIT_NS)) {
@@ -283,15 +273,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
             const uint32_t a_addr = ptx::smem_u32(smem + stage * RING_BYTES);
             const uint32_t b_addr = a_addr + B_OFF;
 #pragma unroll
-            for (int kk = 0; kk < SKT / 32; ++kk) {
+            for (int kk = 0; kk < KT / 32; ++kk) {
               // MN-major, 128-byte swizzle: 8 samples x 128 rows per 1024-byte atom (SBO), the
-              // second 128-row atom of B at +SA (LBO).
+              // second 128-row atom of B at +B_ATOM (LBO).
               const uint64_t ad = ptx::smem_desc(a_addr + kk * 4096, 16, 1024, 2);
-              const uint64_t bd = ptx::smem_desc(b_addr + kk * 4096, SA, 1024, 2);
+              const uint64_t bd = ptx::smem_desc(b_addr + kk * 4096, B_ATOM, 1024, 2);
               ptx::mma_f8f6f4(d, ad, bd, idesc, (ks > k0 || kk > 0) ? 1u : 0u);
               if (WIDE && nb1 > 0) {
-                const uint64_t ad1 = ptx::smem_desc(a_addr + SA + kk * 4096, 16, 1024, 2);
-                const uint64_t bd1 = ptx::smem_desc(b_addr + b1_off + kk * 4096, SA, 1024, 2);
+                const uint64_t ad1 = ptx::smem_desc(a_addr + A_BYTES + kk * 4096, 16, 1024, 2);
+                const uint64_t bd1 = ptx::smem_desc(b_addr + b1_off + kk * 4096, B_ATOM, 1024, 2);
                 ptx::mma_f8f6f4(d + ACC_COLS, ad1, bd1, idesc1, (ks > k0 || kk > 0) ? 1u : 0u);
               }
             }
@@ -397,25 +387,22 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
 
 cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st) {
   {
-    cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<false, KT>), SMEM_BYTES);
-    if (e == cudaSuccess) e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<true, KT>), SMEM_BYTES);
-    if (e == cudaSuccess) e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<true, KT / 2>), SMEM_BYTES);
+    cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<false>), SMEM_BYTES);
+    if (e == cudaSuccess) e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<true>), SMEM_BYTES);
     if (e != cudaSuccess) return e;
   }
   if (args.n_items == 0 || args.T_run == 0) return cudaSuccess;
   const int grid = (int)(args.n_items < num_sms ? args.n_items : num_sms);
-  if (args.wide && args.short_stages)
-    f8_xeng_kernel<true, KT / 2><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
-  else if (args.wide)
-    f8_xeng_kernel<true, KT><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
+  if (args.wide)
+    f8_xeng_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
   else
-    f8_xeng_kernel<false, KT><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
+    f8_xeng_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(args);
   return cudaGetLastError();
 }
 
 std::vector<F8Tile> f8_tile_plan(int N, int R, int plan) {
   std::vector<F8Tile> t;
-  if (plan == 2 || plan == 3) {
+  if (plan == 2) {
     for (int c0 = 0; c0 < N; c0 += 128)
       for (int a0 = c0; a0 < N; a0 += 128) {
         F8Tile x;
@@ -495,12 +482,12 @@ int encode_input_tensor_map(CUtensorMap* map, const void* d_in, int N, int C, in
   return 0;
 }
 
-int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err, int box_t) {
+int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err) {
   encode_fn_t fn = encode_fn(err);
   if (!fn) return -1;
   const cuuint64_t dims[3] = {(cuuint64_t)R, (cuuint64_t)T_pad, (cuuint64_t)C};
   const cuuint64_t strides[2] = {(cuuint64_t)R, (cuuint64_t)R * (cuuint64_t)T_pad};
-  const cuuint32_t box[3] = {128, (cuuint32_t)box_t, 1};
+  const cuuint32_t box[3] = {128, (cuuint32_t)KT, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, d_op, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -108,7 +108,7 @@ def test_pfb_coeffs_match_the_oracle(lib):
         lib.corr_pfb_coeffs(100, 4)
 
 
-@pytest.mark.parametrize("plan", [0, 1, 2, 3])
+@pytest.mark.parametrize("plan", [0, 1, 2])
 def test_tile_plans_cover_the_triangle_exactly_once(plan):
     """Host logic of the tensor path's work decomposition: for every input count, the tiles of a
     channel (both halves of a plan-2 pair) cover each pair a >= c of real inputs exactly once, stay
@@ -120,10 +120,10 @@ def test_tile_plans_cover_the_triangle_exactly_once(plan):
         seen = np.zeros((N, N), dtype=np.int32)
         for c0, a0, nb, extra in corr.corr_tile_plan(N, plan):
             halves = [(c0, a0, nb)]
-            if plan >= 2 and extra & 0xFFFF:
+            if plan == 2 and extra & 0xFFFF:
                 halves.append((c0 + 64, a0 + 64 * (extra >> 16), extra & 0xFFFF))
             else:
-                assert extra == 0 or plan >= 2
+                assert extra == 0 or plan == 2
             for cc, aa, w in halves:
                 assert w in (128, 256) and cc % 64 == 0 and aa % 64 == 0
                 assert 2 * aa + w <= R and 2 * cc + 128 <= R, (N, plan, cc, aa, w)
@@ -136,9 +136,7 @@ def test_tile_plans_cover_the_triangle_exactly_once(plan):
     with pytest.raises(corr.CorrError):
         corr.corr_tile_plan(0, plan)
     with pytest.raises(corr.CorrError):
-        corr.corr_tile_plan(8, 4)
-    if plan == 3:  # plan 3 runs plan 2's items through a finer ring
-        assert corr.corr_tile_plan(300, 3) == corr.corr_tile_plan(300, 2)
+        corr.corr_tile_plan(8, 3)
 
 
 def test_batch_launch_length_rule():

@@ -70,7 +70,15 @@ def profiled_traffic(kernel_files, profile_md, blocks_per_launch, tile_plan=None
 
 
 XENG_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"]
+PAIR_SOURCES = ["xeng_pair.cu", "f8_common.cuh", "ptx_sm100.cuh"]
 PREP_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh"]
+
+
+def xeng_profile(tile_plan):
+    """(kernel name, its sources, its ncu summary in profiles/) for the X-engine of a tile plan."""
+    if tile_plan == 3:
+        return "f8_xeng_pair_kernel", PAIR_SOURCES, "f8_xeng_pair_512in_128ch_8192.md"
+    return "f8_xeng_kernel", XENG_SOURCES, "f8_xeng_512in_128ch_8192.md"
 
 
 def step_traffic(xeng_launches, prep_launches, blocks_per_launch, tile_plan):
@@ -82,7 +90,8 @@ def step_traffic(xeng_launches, prep_launches, blocks_per_launch, tile_plan):
     acc = N_CHAN * corr.corr_n_baselines(N_IN, N_POL) * N_POL * N_POL * 2 * 8
     inp = T_BLOCK * N_BLOCKS * N_CHAN * N_IN
     alg = inp + xeng_launches * 2 * acc + acc
-    x = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch, tile_plan)
+    _, x_src, x_md = xeng_profile(tile_plan)
+    x = profiled_traffic(x_src, x_md, blocks_per_launch, tile_plan)
     pr = profiled_traffic(PREP_SOURCES, "f8_prep_512in_128ch_8192.md", 1)
     out = {"algorithmic_bytes": alg, "xeng_bytes_per_launch": x, "prep_bytes_per_launch": pr,
            "xeng_launches": xeng_launches, "prep_launches": prep_launches}
@@ -121,10 +130,13 @@ def run_extras():
 def issued_flops_per_sample(n_inputs, n_chans, plan=0):
     """MMA flops the tensor path issues per sample under a tile plan (M = 128 instructions of N = nb
     columns; plan 2 items carry a second half of nb1 = extra & 0xFFFF columns), split into wide
-    (N = 256) and narrow (N <= 128) instructions."""
+    (N = 256) and narrow (N <= 128) instructions. A plan-3 item is one M = 256, N = 256 instruction on
+    an SM pair: per SM the work of an M = 128, N = 256 one, counted as two wide instructions."""
     from paper_1411_3751_gb300 import corr
 
     wide = narrow = 0
+    if plan == 3:
+        return 2 * 256 * 256 * n_chans * len(corr.corr_tile_plan(n_inputs, 3)), 0
     for _c0, _a0, nb, extra in corr.corr_tile_plan(n_inputs, plan):
         for n in (nb, (extra & 0xFFFF) if plan == 2 else 0):
             if n > 128:
@@ -322,6 +334,8 @@ def main():
                     help="skip the flush-overhead, grouped-launch, streaming and small-array measurements")
     ap.add_argument("--no-probe", action="store_true", help="skip the tcgen05 issue-rate probe")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default batch schedule")
+    ap.add_argument("--tile-plan", type=int, default=-1,
+                    help="tile plan of the tensor path (0-3; -1: the library default, then the autotuner)")
     ap.add_argument("--prep-sms", type=int, default=-1,
                     help="SMs building the next launch's operand beside the X-engine (-1 library default, 0 none)")
     args = ap.parse_args()
@@ -358,8 +372,10 @@ def main():
     torch.cuda.synchronize()
     xc = corr.Correlator(N_IN, N_CHAN, T_BLOCK, N_POL, path=args.path)
     xc.set_prep_sms(args.prep_sms)
+    if args.tile_plan >= 0 and args.path.startswith("fp8tc"):
+        xc.set_tile_plan(args.tile_plan)
     tuning = None
-    if args.path == "fp8tc" and not args.no_autotune and args.prep_sms == -1:
+    if args.path == "fp8tc" and not args.no_autotune and args.prep_sms == -1 and args.tile_plan < 0:
         # the batch schedule (tile plan, blocks per launch, concurrent build SMs) timed on these blocks
         tuning = xc.autotune(blocks, reps=2)
     xc_plan = xc.tile_plan if args.path.startswith("fp8tc") else 0
@@ -439,10 +455,11 @@ def main():
     else:
         sm_share = 1.0
     traffic = None
+    x_kernel, x_src, x_md = xeng_profile(xc_plan)
     if args.path == "fp8tc":
-        traffic = profiled_traffic(XENG_SOURCES, "f8_xeng_512in_128ch_8192.md", blocks_per_launch, xc_plan)
+        traffic = profiled_traffic(x_src, x_md, blocks_per_launch, xc_plan)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": {"fp8tc": "f8_xeng_kernel", "fp8tc_fused": "f8_fused_kernel",
+            "traffic": traffic, "kernel": {"fp8tc": x_kernel, "fp8tc_fused": "f8_fused_kernel",
                                            "i8mma": "xeng_i8mma_kernel"}.get(args.path, "xeng_fp32_kernel"),
             "peak_source": peak_note, "launch_ms": per_launch_ms,
             "algorithmic": "8 flop x N(N+1)/2 x C x T per launch = %.3e flop (%.0f blocks of 8192 samples per launch)"

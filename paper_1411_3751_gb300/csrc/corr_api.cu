@@ -320,8 +320,8 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
 
 int set_tile_plan(corr_ctx* c, int plan) {
   // the fused path has no wide mode: it keeps plan 0 under plan 2
-  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan == 2 ? 0 : plan);
-  const std::vector<F8Tile> tw = plan == 2 ? f8_tile_plan(c->L.s.N, c->L.R, 2) : t8;
+  const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, plan >= 2 ? 0 : plan);
+  const std::vector<F8Tile> tw = plan >= 2 ? f8_tile_plan(c->L.s.N, c->L.R, plan) : t8;
   std::vector<WorkItem> items;
   items.reserve((size_t)c->L.s.C * tw.size());
   for (int f = 0; f < c->L.s.C; ++f)
@@ -352,6 +352,13 @@ int set_tile_plan(corr_ctx* c, int plan) {
 }
 
 
+int default_tile_plan(int N) {
+  // measured at 512 inputs, 128 channels, 4 x 8192 samples per launch: plan 3 1.35-1.37 ms per launch,
+  // plan 0 1.44-1.46 ms; below 512 inputs the 128-input tiles of plan 3 waste a larger share of their
+  // products on the diagonal (a quarter of them at 256 inputs against a tenth at 512)
+  return N >= 512 ? 3 : 0;
+}
+
 XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush) {
   XengArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -367,6 +374,7 @@ XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flu
   a.flush_len = flush;
   a.err = c->d_err;
   a.wide = c->tile_plan == 2 ? 1 : 0;
+  a.pair = c->tile_plan == 3 ? 1 : 0;
   return a;
 }
 
@@ -514,7 +522,7 @@ int accumulate_batch_overlap(corr_ctx* c, const uint8_t* const* blocks, int n, c
 int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
   // overlapped schedule when there are at least two chunks and the TMA build takes the shape
   const int k = prep_sms_for(c);
-  if (k > 0 && k <= c->num_sms && n > c->L.K_batch && c->tile_plan != 2) {
+  if (k > 0 && k <= c->num_sms && n > c->L.K_batch && c->tile_plan < 2) {
     bool ok = true;
     for (int b = 0; b < n && ok; ++b) ok = f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
     if (ok) {
@@ -646,7 +654,8 @@ corr_ctx* corr_create(int n_inputs, int n_chans, int n_time_per_block, int n_pol
     cuda_fail(e, "corr_create: initialisation");
     return nullptr;
   }
-  if (set_tile_plan(c, 0) != CORR_OK || ensure_operand_scratch(c) != CORR_OK) {
+  c->plan_default = default_tile_plan(L.s.N);
+  if (set_tile_plan(c, c->plan_default) != CORR_OK || ensure_operand_scratch(c) != CORR_OK) {
     const std::string msg = g_err;
     free_ctx(c);
     fail(CORR_ERR_OOM, "corr_create: " + msg);
@@ -676,7 +685,7 @@ int corr_get_path(const corr_ctx* c) { return c ? resolved_path(c) : CORR_ERR_AR
 
 int corr_set_tile_plan(corr_ctx* c, int plan) {
   if (!c) return fail(CORR_ERR_ARG, "corr_set_tile_plan: NULL context");
-  if (plan < 0 || plan > 2) return fail(CORR_ERR_ARG, "corr_set_tile_plan: plan must be 0, 1 or 2");
+  if (plan < 0 || plan > 3) return fail(CORR_ERR_ARG, "corr_set_tile_plan: plan must be 0, 1, 2 or 3");
   // the work lists are read by queued launches: replace them once those are done
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "corr_set_tile_plan: synchronize");
@@ -773,21 +782,21 @@ int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int re
       return cuda_fail(cudaGetLastError(), "corr_autotune: events");
     bool tma_ok = true;
     for (int b = 0; b < n_blocks; ++b) tma_ok = tma_ok && f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
-    // candidates: the default schedule (plan 0, the default launch length, sequential) first; another
-    // replaces the best so far only when it is at least 1% faster, so near-ties keep the default
+    // candidates: the default schedule (the shape's default plan and launch length, sequential) first;
+    // another replaces the best so far only when it is at least 1% faster, so near-ties keep the default
     std::vector<std::tuple<int, int, int>> cand;
-    cand.emplace_back(0, c->K_default, 0);
+    cand.emplace_back(c->plan_default, c->K_default, 0);
     std::vector<int> Ks = {1, 2, 4, 8, c->K_default};
     std::sort(Ks.begin(), Ks.end());
     Ks.erase(std::unique(Ks.begin(), Ks.end()), Ks.end());
-    for (int plan = 0; plan <= 2; ++plan)
+    for (int plan = 0; plan <= 3; ++plan)
       for (int K : Ks) {
         if (K > max_batch_blocks(c) || (K > n_blocks && K != c->K_default)) continue;
-        const std::vector<int> preps = (tma_ok && plan != 2 && n_blocks > K)
+        const std::vector<int> preps = (tma_ok && plan < 2 && n_blocks > K)
                                            ? std::vector<int>{0, c->num_sms / 4, c->num_sms}
                                            : std::vector<int>{0};
         for (int prep : preps)
-          if (!(plan == 0 && K == c->K_default && prep == 0)) cand.emplace_back(plan, K, prep);
+          if (!(plan == c->plan_default && K == c->K_default && prep == 0)) cand.emplace_back(plan, K, prep);
       }
     best_ms = 1e300;
     for (const auto& cd : cand) {
@@ -847,8 +856,8 @@ int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int re
 }
 
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles) {
-  if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 2 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))
-    return fail(CORR_ERR_ARG, "corr_tile_plan: need 1 <= n_inputs <= 2^20, plan 0..2, a buffer for max_tiles > 0");
+  if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 3 || max_tiles < 0 || (max_tiles > 0 && !tiles_out))
+    return fail(CORR_ERR_ARG, "corr_tile_plan: need 1 <= n_inputs <= 2^20, plan 0..3, a buffer for max_tiles > 0");
   const int R = (int)round_up(2LL * n_inputs, kF8RowAlign);
   const std::vector<F8Tile> t = f8_tile_plan(n_inputs, R, plan);
   if (t.size() > (size_t)0x7fffffff) return fail(CORR_ERR_ARG, "corr_tile_plan: too many tiles");

@@ -67,6 +67,7 @@ struct corr_ctx {
   corr::WorkItem* d_items;       // channel-major work list of the two-pass tensor path
   long long n_items;
   int tile_plan;
+  int plan_default;              // default_tile_plan(N): the plan a new context starts with
   void* d_stage[2];      // host dumps
   void* d_in_stage[2];   // host inputs
   size_t in_stage;
@@ -96,6 +97,8 @@ bool timer_begin(corr_ctx* c, int k, cudaStream_t st);
 void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun);
 // tile list and channel-major work list of the tensor paths for plan 0, 1 or 2
 int set_tile_plan(corr_ctx* c, int plan);
+// Tile plan a context of N inputs starts with: 3 (SM pairs) from 512 inputs, else 0.
+int default_tile_plan(int N);
 // blocks per tensor-core launch of batches (reallocates the operand buffers once the device is idle)
 int set_batch_blocks(corr_ctx* c, int K);
 // largest blocks per launch the operand buffer cap allows for this shape

@@ -73,8 +73,8 @@ int group_build_items(corr_group* g) {
   std::vector<WorkItem> items;
   for (int i : order) {
     corr_ctx* c = g->ctx[i];
-    // group launches run the default mode: a member on plan 2 joins with plan 0
-    const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan == 2 ? 0 : c->tile_plan);
+    // group launches run the one-SM mode: a member on plan 2 or 3 joins with plan 0
+    const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan >= 2 ? 0 : c->tile_plan);
     for (int f = 0; f < c->L.s.C; ++f)
       for (const F8Tile& t : t8) items.push_back(WorkItem{i, f, t.c0, t.a0, t.nb, 0});
   }

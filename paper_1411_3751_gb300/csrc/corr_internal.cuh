@@ -74,6 +74,7 @@ struct XengArgs {
   int flush_len;  // samples per in-chip partial sum
   int* err;
   int wide;       // items are c-block pairs of tile plan 2 (see f8_tile_plan)
+  int pair;       // items are the 128 x 128-input tiles of tile plan 3, multiplied on SM pairs
 };
 
 constexpr int kF8Kt = 128;             // time samples per pipeline stage
@@ -144,6 +145,8 @@ cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st);
 // width, pad = half 1's width | (1 << 16 when half 1 starts at the second B atom, on a diagonal
 // pair); half 1's width is 0 when c0 + 64 >= N.
 std::vector<F8Tile> f8_tile_plan(int N, int R, int plan);
+// Tile plan 3 on pairs of SMs (xeng_pair.cu): called by launch_f8_xeng for XengArgs::pair.
+cudaError_t launch_f8_xeng_pair(const XengArgs& args, int num_sms, cudaStream_t st);
 
 size_t f8_smem_bytes();
 

@@ -391,6 +391,7 @@ cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st) {
     if (e == cudaSuccess) e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_kernel<true>), SMEM_BYTES);
     if (e != cudaSuccess) return e;
   }
+  if (args.pair) return launch_f8_xeng_pair(args, num_sms, st);
   if (args.n_items == 0 || args.T_run == 0) return cudaSuccess;
   const int grid = (int)(args.n_items < num_sms ? args.n_items : num_sms);
   if (args.wide)
@@ -402,6 +403,18 @@ cudaError_t launch_f8_xeng(const XengArgs& args, int num_sms, cudaStream_t st) {
 
 std::vector<F8Tile> f8_tile_plan(int N, int R, int plan) {
   std::vector<F8Tile> t;
+  if (plan == 3) {  // 128 c-inputs x 128 a-inputs per item, on a pair of SMs (xeng_pair.cu)
+    for (int c0 = 0; c0 < N; c0 += 128)
+      for (int a0 = c0; a0 < N; a0 += 128) {
+        F8Tile x;
+        x.c0 = c0;
+        x.a0 = a0;
+        x.nb = 256;
+        x.pad = 0;
+        t.push_back(x);
+      }
+    return t;
+  }
   if (plan == 2) {
     for (int c0 = 0; c0 < N; c0 += 128)
       for (int a0 = c0; a0 < N; a0 += 128) {

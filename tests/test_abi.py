@@ -108,11 +108,12 @@ def test_pfb_coeffs_match_the_oracle(lib):
         lib.corr_pfb_coeffs(100, 4)
 
 
-@pytest.mark.parametrize("plan", [0, 1, 2])
+@pytest.mark.parametrize("plan", [0, 1, 2, 3])
 def test_tile_plans_cover_the_triangle_exactly_once(plan):
     """Host logic of the tensor path's work decomposition: for every input count, the tiles of a
-    channel (both halves of a plan-2 pair) cover each pair a >= c of real inputs exactly once, stay
-    within the padded operand rows, and use the MMA widths 128 and 256 only."""
+    channel (both halves of a plan-2 pair, both SMs of a plan-3 pair) cover each pair a >= c of real
+    inputs exactly once, start within the padded operand rows (plans 0-2 also end within them), and
+    use the MMA widths 128 and 256 only."""
     from paper_1411_3751_gb300 import corr
 
     for N in list(range(1, 200)) + [255, 256, 257, 383, 384, 511, 512, 513, 640, 1000, 1024]:
@@ -122,11 +123,17 @@ def test_tile_plans_cover_the_triangle_exactly_once(plan):
             halves = [(c0, a0, nb)]
             if plan == 2 and extra & 0xFFFF:
                 halves.append((c0 + 64, a0 + 64 * (extra >> 16), extra & 0xFFFF))
+            elif plan == 3:
+                assert nb == 256 and extra == 0 and c0 % 128 == 0 and a0 % 128 == 0
+                halves.append((c0 + 64, a0, nb))  # the pair's second SM: the next 64 c-inputs
             else:
                 assert extra == 0 or plan == 2
             for cc, aa, w in halves:
                 assert w in (128, 256) and cc % 64 == 0 and aa % 64 == 0
-                assert 2 * aa + w <= R and 2 * cc + 128 <= R, (N, plan, cc, aa, w)
+                if plan == 3:  # rows past R are read as zeros (inputs >= N)
+                    assert 2 * aa < R and 2 * c0 < R, (N, plan, cc, aa, w)
+                else:
+                    assert 2 * aa + w <= R and 2 * cc + 128 <= R, (N, plan, cc, aa, w)
                 c = np.arange(cc, min(cc + 64, N))[:, None]
                 a = np.arange(aa, min(aa + w // 2, N))[None, :]
                 m = (a >= c)
@@ -136,7 +143,7 @@ def test_tile_plans_cover_the_triangle_exactly_once(plan):
     with pytest.raises(corr.CorrError):
         corr.corr_tile_plan(0, plan)
     with pytest.raises(corr.CorrError):
-        corr.corr_tile_plan(8, 3)
+        corr.corr_tile_plan(8, 4)
 
 
 def test_batch_launch_length_rule():

@@ -48,7 +48,10 @@ def _correlate(env, x_host, npol, path, flush, blocks=1, block_t=None):
     T, C, N = x_host.shape
     bt = T if block_t is None else block_t
     d = torch.from_numpy(x_host).cuda()
+    path, _, plan = path.partition("/plan")  # "fp8tc/plan3": the tensor path on SM pairs
     with corr.Correlator(N, C, bt, npol, path=path) as xc:
+        if plan:
+            xc.set_tile_plan(int(plan))
         xc.set_flush_period(flush)
         for b in range(blocks):
             for t0 in range(0, T, bt):
@@ -60,7 +63,8 @@ def _correlate(env, x_host, npol, path, flush, blocks=1, block_t=None):
     return cross, autos
 
 
-CASES = [("fp8tc", T_FLUSH), ("fp8tc_fused", T_FLUSH), ("fp32", T_FLUSH), ("i8mma", 16384), ("i8mma", T_FLUSH)]
+CASES = [("fp8tc", T_FLUSH), ("fp8tc/plan3", T_FLUSH), ("fp8tc_fused", T_FLUSH), ("fp32", T_FLUSH), ("i8mma", 16384),
+         ("i8mma", T_FLUSH)]
 
 
 @pytest.mark.parametrize("path,flush", CASES)
@@ -110,7 +114,7 @@ def test_high_magnitude_one_full_flush(env, path, flush):
     assert np.array_equal(got_a, want_a)
 
 
-@pytest.mark.parametrize("path", ["fp8tc", "fp8tc_fused", "fp32", "i8mma"])
+@pytest.mark.parametrize("path", ["fp8tc", "fp8tc/plan3", "fp8tc_fused", "fp32", "i8mma"])
 @pytest.mark.parametrize("n_inputs", [2, 64])
 @pytest.mark.parametrize("value", [(-8, -8), (7, 7)])
 def test_int64_sums_past_2_31(env, path, n_inputs, value):
@@ -121,7 +125,10 @@ def test_int64_sums_past_2_31(env, path, n_inputs, value):
     corr, _, torch = env
     N, C, T, npol, blocks = n_inputs, 1, T_FLUSH, 2, 512
     d = torch.full((T, C, N), int(_byte(*value)), dtype=torch.uint8, device="cuda")
+    path, _, plan = path.partition("/plan")
     with corr.Correlator(N, C, T, npol, path=path) as xc:
+        if plan:
+            xc.set_tile_plan(int(plan))
         for _ in range(blocks):
             xc.accumulate(d)
         cross = xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy()

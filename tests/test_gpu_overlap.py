@@ -27,6 +27,7 @@ def env():
 def _batch(env, host_blocks, N, C, T, npol, prep_sms):
     corr, _, torch = env
     with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+        xc.set_tile_plan(0)  # the overlapped schedule runs the one-SM plans (0 and 1)
         xc.set_prep_sms(prep_sms)
         assert xc.prep_sms == prep_sms
         blocks = [torch.from_numpy(b).cuda() for b in host_blocks]
@@ -83,6 +84,7 @@ def test_overlap_then_single_blocks_and_dumps_in_order(env):
     host = synth.generate_host(spec, (2 * nb + 1) * T, C, N)
     blk = [torch.from_numpy(np.ascontiguousarray(host[b * T:(b + 1) * T])).cuda() for b in range(2 * nb + 1)]
     with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+        xc.set_tile_plan(0)
         xc.set_prep_sms(24)
         xc.accumulate_batch(blk[:nb])
         xc.accumulate(blk[nb])

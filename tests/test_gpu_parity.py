@@ -103,21 +103,22 @@ def test_empty_context_and_empty_batch(env, path):
     assert np.array_equal(cross, want_c) and np.array_equal(autos, want_a)
 
 
-@pytest.mark.parametrize("plan", [1, 2])
+@pytest.mark.parametrize("plan", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", [(512, 2, 640, 2), (200, 3, 1000, 2), (130, 2, 300, 2), (64, 3, 4096, 1),
                                    (258, 2, 256, 2), (6, 2, 33, 1), (1, 1, 5, 1), (96, 1, 129, 2), (2048, 1, 256, 2),
                                    (192, 2, 384, 1)])
 def test_tile_plans(env, plan, shape):
-    """The other work-item plans of the two-pass tensor path are bit-exact: plan 1 (64 x 64 tiles) and
+    """Every work-item plan of the two-pass tensor path is bit-exact: plan 0 (64 x 128 tiles), plan 1 (64 x 64 tiles),
     plan 2 (pairs of 64-input c-blocks sharing one operand tile; a half-width second half on the
-    diagonal, none when the pair's second c-block lies past N). Three blocks, flushed every 128
+    diagonal, none when the pair's second c-block lies past N) and plan 3 (128 x 128-input tiles on
+    pairs of SMs, operand rows past the padded rows read as zeros). Three blocks, flushed every 128
     samples (one ring stage: the accumulator handoff at every stage), then a plain block."""
     corr, synth, torch = env
     N, C, T, npol = shape
     host = synth.generate_host(synth.Spec(kind="saturate", seed=N * 7 + T, seg_len=128, m8_segment=1), 4 * T, C, N)
     want_c, want_a = oracle.correlate(host, npol, threads=8)
     with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
-        assert xc.tile_plan == 0
+        assert xc.tile_plan == (3 if N >= 512 else 0)  # the default: SM pairs from 512 inputs
         xc.set_tile_plan(plan)
         assert xc.tile_plan == plan
         xc.set_flush_period(128)
@@ -127,22 +128,23 @@ def test_tile_plans(env, plan, shape):
         c = xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy()
         a = xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy()
         xc.sync()
-        for bad in (-1, 3):
+        for bad in (-1, 4):
             with pytest.raises(corr.CorrError):
                 xc.set_tile_plan(bad)
         assert xc.tile_plan == plan
     assert np.array_equal(c, want_c) and np.array_equal(a, want_a)
 
 
-def test_tile_plan_2_full_size_sampled(env):
-    """Plan 2 at the benchmark's size (512 inputs, 128 channels, 4 blocks of 8192 samples, one launch):
-    oracle cells on two regenerated channels and the oracle autos of every channel."""
+@pytest.mark.parametrize("plan", [2, 3])
+def test_tile_plan_full_size_sampled(env, plan):
+    """Plans 2 and 3 at the benchmark's size (512 inputs, 128 channels, 4 blocks of 8192 samples, one
+    launch): oracle cells on two regenerated channels and the oracle autos of every channel."""
     corr, synth, torch = env
     N, C, T, B = 512, 128, 8192, 4
     spec = synth.Spec(kind="gauss_tone", seed=0x14113751 + 2)
     blocks = [synth.generate_device(spec, T, C, N, t0=b * T) for b in range(B)]
     with corr.Correlator(N, C, T, 2, path="fp8tc") as xc:
-        xc.set_tile_plan(2)
+        xc.set_tile_plan(plan)
         xc.accumulate_batch(blocks)
         c = xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy()
         a = xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy()

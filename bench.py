@@ -71,7 +71,7 @@ def profiled_traffic(kernel_files, profile_md, blocks_per_launch, tile_plan=None
 
 XENG_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh", "ptx_sm100.cuh"]
 PAIR_SOURCES = ["xeng_pair.cu", "f8_common.cuh", "ptx_sm100.cuh"]
-PREP_SOURCES = ["xeng_fp8tc.cu", "f8_common.cuh"]
+PREP_SOURCES = ["f8_prep.cu", "f8_common.cuh"]
 
 
 def xeng_profile(tile_plan):

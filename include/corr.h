@@ -107,13 +107,17 @@ int corr_get_path(const corr_ctx* ctx);
 
 /*
  * corr_set_tile_plan - how the two-pass tensor path cuts the triangle a >= c of each channel
- * (Sec. 2.5's pairwise products) into work items: 0 (default) tiles of 64 c-inputs x 128 a-inputs
- * (64 on the diagonal); 1 tiles of 64 x 64; 2 pairs of 64-input c-blocks against 128 a-inputs, the
+ * (Sec. 2.5's pairwise products) into work items: 0 tiles of 64 c-inputs x 128 a-inputs (64 on the
+ * diagonal), one SM each; 1 tiles of 64 x 64; 2 pairs of 64-input c-blocks against 128 a-inputs, the
  * two halves sharing one operand tile (a third fewer operand bytes per product; the pair fills both
- * TMEM accumulators, so its drain is not overlapped with the next item). Results are identical for
- * every plan. Waits for the device (queued launches read the current work list). CORR_ERR_ARG for
- * another value. Group launches (corr_group_*) always use plan 0 or 1. corr_get_tile_plan returns
- * the current plan (CORR_ERR_ARG for a NULL context).
+ * TMEM accumulators, so its drain is not overlapped with the next item); 3 tiles of 128 c-inputs x
+ * 128 a-inputs on a pair of SMs (a cluster of two CTAs sharing 2-SM tensor instructions: each SM
+ * fetches a third fewer operand bytes for the same work; the diagonal tiles compute a quarter of
+ * their products for nothing). A new context starts on plan 3 from 512 inputs and on plan 0 below.
+ * Results are identical for every plan. Waits for the device (queued launches read the current work
+ * list). CORR_ERR_ARG for another value. Group launches (corr_group_*) always use plan 0 or 1, and the
+ * overlapped build (corr_set_prep_sms) runs with plans 0 and 1 only. corr_get_tile_plan returns the
+ * current plan (CORR_ERR_ARG for a NULL context).
  */
 int corr_set_tile_plan(corr_ctx* ctx, int plan);
 int corr_get_tile_plan(const corr_ctx* ctx);
@@ -123,10 +127,11 @@ int corr_get_tile_plan(const corr_ctx* ctx);
  * device call): returns the number of tiles and writes up to max_tiles of them to tiles_out as
  * int[4] (c0, a0, nb, extra). A tile covers c-inputs c0 .. c0 + 63 against a-inputs a0 .. a0 + nb / 2
  * - 1 (nb operand rows, two per input). For plan 2, extra = nb1 | (hi << 16) describes its second half:
- * c-inputs c0 + 64 .. c0 + 127 against nb1 / 2 a-inputs from a0 + 64 hi; otherwise extra = 0.
- * Together the tiles cover every pair a >= c of the triangle exactly once (inputs >= n_inputs are
- * padding). CORR_ERR_ARG for n_inputs outside 1 .. 2^20, plan outside 0 .. 2, or max_tiles > 0 with
- * a NULL buffer.
+ * c-inputs c0 + 64 .. c0 + 127 against nb1 / 2 a-inputs from a0 + 64 hi; otherwise extra = 0. A plan-3
+ * tile (nb = 256) covers c-inputs c0 .. c0 + 127 against a-inputs a0 .. a0 + 127, the pair's second SM
+ * taking c0 + 64 .. c0 + 127. Together the tiles cover every pair a >= c of the triangle exactly once
+ * (inputs >= n_inputs are padding). CORR_ERR_ARG for n_inputs outside 1 .. 2^20, plan outside 0 .. 3,
+ * or max_tiles > 0 with a NULL buffer.
  */
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
 
@@ -138,7 +143,7 @@ int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
  * runs beside the X-engine on every SM. The first build and the last multiply use the whole GPU. The
  * first such batch allocates a second operand buffer of the first one's size (see
  * corr_footprint_bytes); if that fails, or the shape does not suit the TMA build (n_inputs % 16 != 0,
- * n_inputs < 128, T < 128, a tile plan of 2, or a block not 16-byte aligned), batches run the two
+ * n_inputs < 128, T < 128, a tile plan of 2 or 3, or a block not 16-byte aligned), batches run the two
  * passes in sequence. 0 runs them in sequence always; -1 (the default) is the automatic choice, which
  * on GB300 is 0: the X-engine saturates each SM's memory paths and a concurrent build slows it by more
  * than the build's own time. Results are identical either way. CORR_ERR_ARG outside -1 .. SMs.
@@ -171,12 +176,13 @@ typedef struct corr_tuning {
 /*
  * corr_autotune - times the two-pass tensor path's schedules on the caller's own n_blocks device
  * blocks (uint8[T][C][N] each; the batch of corr_accumulate_batch) and keeps the fastest for this
- * context: tile plan 0, 1 or 2 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
+ * context: tile plan 0, 1, 2 or 3 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
  * the operand cap) x SMs of a concurrent operand build (0, a quarter of the SMs, all of them; only for
  * batches of several launches on shapes the build takes). Each schedule runs the batch once to warm up
- * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream; the default schedule is timed
- * first and another replaces the best only when at least 1% faster. The results are cached in-process
- * by (N, C, T, n_pol, SMs, n_blocks), and in the file named by CORR_AUTOTUNE_CACHE if set; a cached
+ * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream; the default schedule (the
+ * shape's default plan) is timed first and another replaces the best only when at least 1% faster.
+ * The results are cached in-process by (N, C, T, n_pol, SMs, n_blocks), and in the file named by
+ * CORR_AUTOTUNE_CACHE if set; a cached
  * choice is applied without timing. Afterwards the accumulators and sample counts are zero (the trials
  * added into them). Synchronizes the device. out (optional) receives the choice. No counterpart in the
  * paper. CORR_ERR_STATE unless the context runs the two-pass tensor path.

@@ -19,7 +19,7 @@ OUT = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"] + ARCH
 
-CORR_SOURCES = ["corr_api.cu", "xeng_fp32.cu", "xeng_i8mma.cu", "xeng_fp8tc.cu", "xeng_f8fused.cu", "autos_dump.cu", "requant.cu", "pfb.cu", "corr_static.cu", "selftest.cu", "corr_group.cu", "probe.cu", "corner_turn.cu", "prep_tma.cu", "xeng_pair.cu"]
+CORR_SOURCES = ["corr_api.cu", "xeng_fp32.cu", "xeng_i8mma.cu", "xeng_fp8tc.cu", "f8_prep.cu", "xeng_f8fused.cu", "autos_dump.cu", "requant.cu", "pfb.cu", "corr_static.cu", "selftest.cu", "corr_group.cu", "probe.cu", "corner_turn.cu", "prep_tma.cu", "xeng_pair.cu"]
 
 LIBCORR = os.path.join(OUT, "libcorr.so")
 LIBSYNTH_CUDA = os.path.join(OUT, "libcorrsynth_cuda.so")

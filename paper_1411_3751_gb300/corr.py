@@ -467,7 +467,8 @@ class Correlator:
         return corr_autotune(self.ctx, [b.data_ptr() for b in blocks], reps, _stream_handle(stream))
 
     def set_tile_plan(self, plan: int):
-        """Work-item plan of the two-pass tensor path (0 default, 1, 2: c-block pairs)."""
+        """Work-item plan of the two-pass tensor path (0: 64 x 128-input tiles, 1: 64 x 64, 2: c-block
+        pairs, 3: 128 x 128-input tiles on SM pairs; a new context starts on 3 from 512 inputs, else 0)."""
         corr_set_tile_plan(self.ctx, plan)
 
     @property

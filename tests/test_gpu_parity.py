@@ -135,6 +135,43 @@ def test_tile_plans(env, plan, shape):
     assert np.array_equal(c, want_c) and np.array_equal(a, want_a)
 
 
+@pytest.mark.parametrize("N", [512, 200, 6])
+def test_offset_and_signed_paths_in_one_integration(env, N):
+    """The FP8 tensor paths multiply offset samples (corrected at the dump with the per-input offset sums
+    of the blocks they took) while the int8 and FP32 paths multiply the signed samples. Blocks of both
+    kinds in one integration, on tile plans 0 and 3, single and batched, then a dump with reset and more
+    blocks: every dump equals the oracle over exactly the blocks before it."""
+    corr, synth, torch = env
+    C, T, npol = 3, 1024, 2 if N % 2 == 0 else 1
+    host = synth.generate_host(synth.Spec(kind="saturate", seed=N + 5, seg_len=256, m8_segment=2), 8 * T, C, N)
+    blk = [torch.from_numpy(np.ascontiguousarray(host[b * T:(b + 1) * T])).cuda() for b in range(8)]
+    with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+        xc.set_tile_plan(0)
+        xc.accumulate(blk[0])
+        xc.set_path("i8mma")
+        xc.accumulate(blk[1])
+        xc.set_path("fp8tc")
+        xc.set_tile_plan(3)
+        xc.accumulate_batch(blk[2:4])
+        xc.set_path("fp32")
+        xc.accumulate(blk[4])
+        xc.set_path("fp8tc")
+        xc.accumulate(blk[5])
+        c1 = xc.dump(corr.CORR_WHAT_CROSS, reset=True).cpu().numpy()
+        a1 = xc.dump(corr.CORR_WHAT_AUTO, reset=True).cpu().numpy()
+        xc.set_path("i8mma")
+        xc.accumulate(blk[6])
+        xc.set_path("fp8tc")
+        xc.accumulate(blk[7])
+        c2 = xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy()
+        a2 = xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy()
+        xc.sync()
+    w1c, w1a = oracle.correlate(host[:6 * T], npol, threads=8)
+    w2c, w2a = oracle.correlate(host[6 * T:], npol, threads=8)
+    assert np.array_equal(c1, w1c) and np.array_equal(a1, w1a)
+    assert np.array_equal(c2, w2c) and np.array_equal(a2, w2a)
+
+
 @pytest.mark.parametrize("plan", [2, 3])
 def test_tile_plan_full_size_sampled(env, plan):
     """Plans 2 and 3 at the benchmark's size (512 inputs, 128 channels, 4 blocks of 8192 samples, one

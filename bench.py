@@ -477,6 +477,28 @@ def main():
         roof["frac_useful_of_issue_peak"] = achieved / probe["tflops_n256"]
     if args.path == "fp8tc":
         roof["step_traffic"] = step_traffic(xeng_n / args.steps, unpack_n / args.steps, blocks_per_launch, xc_plan)
+    if args.path == "fp8tc" and prep_sms > 0 and launches_per_batch > 1:
+        # the step overlaps the operand build with the multiply, so the X-engine launches above ran on
+        # fewer SMs beside a build; the same kernel on the same launches with the passes in sequence
+        # (the whole GPU, nothing beside it), timed after the step's timed region
+        xc.set_prep_sms(0)
+        step()
+        xc.sync()
+        xc.profile(True)
+        for _ in range(5):
+            step()
+        xc.sync()
+        iso_ms, iso_n = xc.profile_read(corr.CORR_KERNEL_XENG)
+        xc.profile(False)
+        xc.set_prep_sms(prep_sms)
+        iso_launch = iso_ms / max(1, iso_n)
+        iso = {"launch_ms": iso_launch, "achieved": flops_launch / (iso_launch / 1e3) / 1e12,
+               "what": "the same kernel and launches with the batch's two passes in sequence (whole GPU, no "
+                       "concurrent build), 5 steps after the timed region"}
+        iso["frac"] = iso["achieved"] / peak
+        if probe:
+            iso["frac_issue"] = ideal_ms / iso_launch
+        roof["isolated"] = iso
 
     # end-to-end through the public API from pinned host buffers
     e2e = None

@@ -116,7 +116,7 @@ int corr_get_path(const corr_ctx* ctx);
  * their products for nothing). A new context starts on plan 3 from 512 inputs and on plan 0 below.
  * Results are identical for every plan. Waits for the device (queued launches read the current work
  * list). CORR_ERR_ARG for another value. Group launches (corr_group_*) always use plan 0 or 1, and the
- * overlapped build (corr_set_prep_sms) runs with plans 0 and 1 only. corr_get_tile_plan returns the
+ * overlapped build (corr_set_prep_sms) runs with plans 0, 1 and 3. corr_get_tile_plan returns the
  * current plan (CORR_ERR_ARG for a NULL context).
  */
 int corr_set_tile_plan(corr_ctx* ctx, int plan);
@@ -143,10 +143,13 @@ int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
  * runs beside the X-engine on every SM. The first build and the last multiply use the whole GPU. The
  * first such batch allocates a second operand buffer of the first one's size (see
  * corr_footprint_bytes); if that fails, or the shape does not suit the TMA build (n_inputs % 16 != 0,
- * n_inputs < 128, T < 128, a tile plan of 2 or 3, or a block not 16-byte aligned), batches run the two
- * passes in sequence. 0 runs them in sequence always; -1 (the default) is the automatic choice, which
- * on GB300 is 0: the X-engine saturates each SM's memory paths and a concurrent build slows it by more
- * than the build's own time. Results are identical either way. CORR_ERR_ARG outside -1 .. SMs.
+ * n_inputs < 128, T < 128, tile plan 2, or a block not 16-byte aligned), batches run the two passes in
+ * sequence. 0 runs them in sequence always; -1 (the default) is the automatic choice, 0, and
+ * corr_autotune times the overlapped schedules on the caller's blocks: with tile plan 3 at 512 inputs
+ * the build on about 2/7 of the SMs balances the multiply on the others (+7% measured); with the one-SM
+ * plans the X-engine slows by more than the SMs it gives up. With plan 3, sms == SMs leaves the build
+ * no room beside the X-engine CTAs (it then runs between them). Results are identical either way.
+ * CORR_ERR_ARG outside -1 .. SMs.
  * corr_get_prep_sms returns the SM count in use (the automatic value resolved).
  */
 int corr_set_prep_sms(corr_ctx* ctx, int sms);
@@ -177,8 +180,8 @@ typedef struct corr_tuning {
  * corr_autotune - times the two-pass tensor path's schedules on the caller's own n_blocks device
  * blocks (uint8[T][C][N] each; the batch of corr_accumulate_batch) and keeps the fastest for this
  * context: tile plan 0, 1, 2 or 3 x blocks per launch 1, 2, 4, 8 and the default (within n_blocks and
- * the operand cap) x SMs of a concurrent operand build (0, a quarter of the SMs, all of them; only for
- * batches of several launches on shapes the build takes). Each schedule runs the batch once to warm up
+ * the operand cap) x SMs of a concurrent operand build (0, 1/5, 1/4, 2/7 and 1/3 of the SMs, and all of
+ * them for plans 0 and 1; only for batches of several launches on shapes the build takes). Each schedule runs the batch once to warm up
  * and `reps` (1 .. 100) times timed with CUDA events on cuda_stream; the default schedule (the
  * shape's default plan) is timed first and another replaces the best only when at least 1% faster.
  * The results are cached in-process by (N, C, T, n_pol, SMs, n_blocks), and in the file named by

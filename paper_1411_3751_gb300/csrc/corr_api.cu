@@ -428,9 +428,13 @@ int set_batch_blocks(corr_ctx* c, int K) {
 // SMs that build the next chunk's operand while the X-engine multiplies the current one.
 int prep_sms_for(const corr_ctx* c) {
   if (c->prep_sms >= 0) return c->prep_sms;
-  // automatic: sequential. Measured at 512 inputs x 128 channels x 16 blocks of 8192 samples: 217.7
+  // automatic: sequential; corr_autotune times the overlapped schedules on the caller's blocks.
+  // Measured at 512 inputs x 128 channels x 16 blocks of 8192 samples: with the one-SM plan 0, 217.7
   // Tera-CMAC/s in sequence, 209.4 with the build on 38 SMs of its own, 187.6 with a small build CTA
-  // beside the X-engine on every SM (the X-engine slows by more than the SMs or bandwidth it gives up)
+  // beside the X-engine on every SM (the X-engine slows by more than the SMs it gives up); with the
+  // SM-pair plan 3, 236.3 in sequence and 240.2 / 252.4 / 244.5 with the build on 38 / 42 / 46 SMs
+  // (the X-engine now slows in proportion to the SMs it gives up; the best k balances a build of a
+  // launch's blocks on k SMs against their multiply on the others)
   return 0;
 }
 
@@ -516,13 +520,13 @@ int accumulate_batch_overlap(corr_ctx* c, const uint8_t* const* blocks, int n, c
 // n blocks through the two-pass tensor path in chunks of up to K_batch blocks (launch length from the
 // L2 budget, see kL2Window): the operand of a chunk is built with each block at its own sample
 // offset, then one tensor-core launch multiplies the whole chunk, so blocks share launches and
-// flushes. (Building the next chunk while this one multiplies gains nothing: on a second stream the
-// persistent X-engine holds every SM, and inside it the extra load/store traffic slows its epilogue;
-// the chunks run in order on the caller's stream.)
+// flushes. With prep_sms_for(c) = k > 0 the build of chunk j + 1 runs on k SMs beside the multiply of
+// chunk j (accumulate_batch_overlap); otherwise the chunks run in order on the caller's stream.
 int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cudaStream_t st) {
-  // overlapped schedule when there are at least two chunks and the TMA build takes the shape
+  // overlapped schedule when there are at least two chunks and the TMA build takes the shape (the wide
+  // plan 2 fills both accumulators per item and is not overlapped)
   const int k = prep_sms_for(c);
-  if (k > 0 && k <= c->num_sms && n > c->L.K_batch && c->tile_plan < 2) {
+  if (k > 0 && k <= c->num_sms && n > c->L.K_batch && c->tile_plan != 2) {
     bool ok = true;
     for (int b = 0; b < n && ok; ++b) ok = f8_prep_tma_supported(c->L.s, blocks[b], c->L.s.T);
     if (ok) {
@@ -792,9 +796,16 @@ int corr_autotune(corr_ctx* c, const void* const* d_blocks, int n_blocks, int re
     for (int plan = 0; plan <= 3; ++plan)
       for (int K : Ks) {
         if (K > max_batch_blocks(c) || (K > n_blocks && K != c->K_default)) continue;
-        const std::vector<int> preps = (tma_ok && plan < 2 && n_blocks > K)
-                                           ? std::vector<int>{0, c->num_sms / 4, c->num_sms}
-                                           : std::vector<int>{0};
+        // concurrent build SMs: fractions of the GPU around the balance of a build of K blocks on k
+        // SMs against a multiply of K blocks on the others (about 2/7 at 512 inputs on plan 3), and
+        // for the one-SM plans a small build CTA beside the X-engine on every SM (which the 224 KB
+        // ring of a plan-3 CTA leaves no room for)
+        std::vector<int> preps = {0};
+        if (tma_ok && plan != 2 && n_blocks > K) {
+          const int S = c->num_sms;
+          for (int k : {S / 5, S / 4, 2 * S / 7, S / 3}) preps.push_back(k);
+          if (plan < 2) preps.push_back(S);
+        }
         for (int prep : preps)
           if (!(plan == c->plan_default && K == c->K_default && prep == 0)) cand.emplace_back(plan, K, prep);
       }

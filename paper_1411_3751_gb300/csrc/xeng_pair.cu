@@ -260,10 +260,11 @@ cudaError_t launch_f8_xeng_pair(const XengArgs& args, int num_sms, cudaStream_t 
   cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(f8_xeng_pair_kernel), P_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   if (args.n_items == 0 || args.T_run == 0) return cudaSuccess;
-  long long pairs = std::min<long long>(args.n_items, num_sms / 2);
+  // one pair per two SMs the launch may use (at least one pair: given a single SM it starts when a
+  // second one frees), and no more pairs than fit on the GPU at once
+  long long pairs = std::max<long long>(1, std::min<long long>(args.n_items, num_sms / 2));
   const int fit = max_pairs();
   if (fit > 0) pairs = std::min<long long>(pairs, fit);
-  if (pairs < 1) return cudaErrorInvalidConfiguration;
   f8_xeng_pair_kernel<<<(unsigned)(2 * pairs), P_THREADS, P_SMEM_BYTES, st>>>(args);
   return cudaGetLastError();
 }

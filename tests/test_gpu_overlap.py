@@ -24,10 +24,10 @@ def env():
     return corr, synth, torch
 
 
-def _batch(env, host_blocks, N, C, T, npol, prep_sms):
+def _batch(env, host_blocks, N, C, T, npol, prep_sms, plan=0):
     corr, _, torch = env
     with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
-        xc.set_tile_plan(0)  # the overlapped schedule runs the one-SM plans (0 and 1)
+        xc.set_tile_plan(plan)  # the overlapped schedule runs plans 0, 1 and 3
         xc.set_prep_sms(prep_sms)
         assert xc.prep_sms == prep_sms
         blocks = [torch.from_numpy(b).cuda() for b in host_blocks]
@@ -39,8 +39,11 @@ def _batch(env, host_blocks, N, C, T, npol, prep_sms):
     return c, a, k
 
 
+@pytest.mark.parametrize("plan", [0, 3])
 @pytest.mark.parametrize("shape", [(144, 3, 1000, 2), (256, 2, 4096, 2), (128, 4, 2048, 1)])
-def test_overlapped_batch_matches_oracle_and_sequential(env, shape):
+def test_overlapped_batch_matches_oracle_and_sequential(env, shape, plan):
+    """Tile plan 0 (one SM per item) and plan 3 (SM pairs: the X-engine on S - k SMs is a grid of
+    (S - k) / 2 clusters; with k = S the build has no room beside the pair CTAs and runs between them)."""
     corr, synth, torch = env
     N, C, T, npol = shape
     k = corr.corr_batch_blocks(N, C, T, npol)
@@ -49,19 +52,20 @@ def test_overlapped_batch_matches_oracle_and_sequential(env, shape):
     host = synth.generate_host(spec, n_blocks * T, C, N)
     blocks = [np.ascontiguousarray(host[b * T:(b + 1) * T]) for b in range(n_blocks)]
     want_c, want_a = oracle.correlate(host, npol, threads=8)
-    seq_c, seq_a, _ = _batch(env, blocks, N, C, T, npol, 0)
+    seq_c, seq_a, _ = _batch(env, blocks, N, C, T, npol, 0, plan)
     assert np.array_equal(seq_c, want_c) and np.array_equal(seq_a, want_a)
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
-    for sms in (1, 8, 30, 76, n_sms - 1, n_sms):  # n_sms: a small build CTA beside the X-engine on every SM
-        c, a, _ = _batch(env, blocks, N, C, T, npol, sms)
+    for sms in (1, 8, 30, 43, 76, n_sms - 1, n_sms):  # n_sms: a small build CTA beside the X-engine on every SM
+        c, a, _ = _batch(env, blocks, N, C, T, npol, sms, plan)
         bad = np.argwhere(c != want_c)
         assert bad.size == 0, (sms, bad[:3].tolist())
         assert np.array_equal(a, want_a), sms
 
 
-def test_overlapped_batch_512_inputs(env):
+@pytest.mark.parametrize("plan", [0, 3])
+def test_overlapped_batch_512_inputs(env, plan):
     """The benchmark's shape per launch (512 inputs, 8192-sample blocks, 4 blocks per launch) on two
-    channels, nine blocks: launches of 4, 4 and 1 blocks."""
+    channels, nine blocks: launches of 4, 4 and 1 blocks, the build on 43 SMs (about 2/7 of them)."""
     corr, synth, torch = env
     N, C, T, npol = 512, 2, 8192, 2
     assert corr.corr_batch_blocks(N, C, T, npol) == 4
@@ -69,7 +73,7 @@ def test_overlapped_batch_512_inputs(env):
     host = synth.generate_host(spec, 9 * T, C, N)
     blocks = [np.ascontiguousarray(host[b * T:(b + 1) * T]) for b in range(9)]
     want_c, want_a = oracle.correlate(host, npol, threads=8)
-    c, a, _ = _batch(env, blocks, N, C, T, npol, 30)
+    c, a, _ = _batch(env, blocks, N, C, T, npol, 43, plan)
     assert np.array_equal(c, want_c) and np.array_equal(a, want_a)
 
 

@@ -81,10 +81,12 @@ def xeng_profile(tile_plan):
     return "f8_xeng_kernel", XENG_SOURCES, "f8_xeng_512in_128ch_8192.md"
 
 
-def step_traffic(xeng_launches, prep_launches, blocks_per_launch, tile_plan):
+def step_traffic(xeng_launches, prep_launches, blocks_per_launch, tile_plan, ms_step=None, hbm_gbs=None):
     """DRAM bytes of one step from the ncu captures summarised in profiles/ (per launch, source-hash
     checked) against the algorithmic bytes of the step: the input read once, the int64 cross
-    accumulators read and written once per X-engine launch, and the dumped visibilities written once."""
+    accumulators read and written once per X-engine launch, and the dumped visibilities written once;
+    with the step time, the rate those bytes imply as a share of the measured HBM copy bandwidth (the
+    builds beside the multiply move the same bytes as in sequence)."""
     from paper_1411_3751_gb300 import corr
 
     acc = N_CHAN * corr.corr_n_baselines(N_IN, N_POL) * N_POL * N_POL * 2 * 8
@@ -99,6 +101,9 @@ def step_traffic(xeng_launches, prep_launches, blocks_per_launch, tile_plan):
         dump = 3 * acc  # dump kernels (not captured) at their own algorithmic bytes: read, write, reset
         meas = x * xeng_launches + pr * prep_launches + dump
         out.update({"measured_bytes": meas, "ratio": meas / alg})
+        if ms_step and hbm_gbs:
+            out["step_gbs"] = meas / (ms_step / 1e3) / 1e9
+            out["step_frac_of_hbm"] = out["step_gbs"] / hbm_gbs
     return out
 
 
@@ -476,7 +481,8 @@ def main():
         roof["frac_issue"] = ideal_ms / per_launch_ms
         roof["frac_useful_of_issue_peak"] = achieved / probe["tflops_n256"]
     if args.path == "fp8tc":
-        roof["step_traffic"] = step_traffic(xeng_n / args.steps, unpack_n / args.steps, blocks_per_launch, xc_plan)
+        roof["step_traffic"] = step_traffic(xeng_n / args.steps, unpack_n / args.steps, blocks_per_launch, xc_plan,
+                                            ms_step, peaks.get("hbm_gbs") if peaks else None)
     if args.path == "fp8tc" and prep_sms > 0 and launches_per_batch > 1:
         # the step overlaps the operand build with the multiply, so the X-engine launches above ran on
         # fewer SMs beside a build; the same kernel on the same launches with the passes in sequence

@@ -142,14 +142,21 @@ __global__ void __launch_bounds__(NT) xeng_fp32_kernel(const uint8_t* __restrict
         bnim[2 * h] = pk(n.x, n.y);
         bnim[2 * h + 1] = pk(n.z, n.w);
       }
+      // x_i conj(x_j) = (ar + i ai)(br - i bi): re += ar br + ai bi, im += ai br - ar bi, in two sweeps
+      // so that the two updates of an accumulator pair are 64 instructions apart (no back-to-back
+      // dependence on the FMA latency)
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int p = 0; p < U / 2; ++p) {
-          // x_i conj(x_j) = (ar + i ai)(br - i bi): re += ar br + ai bi, im += ai br - ar bi
           ffma2(are[u][p], ar[u], bre[p]);
-          ffma2(are[u][p], ai[u], bim[p]);
           ffma2(aim[u][p], ai[u], bre[p]);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int p = 0; p < U / 2; ++p) {
+          ffma2(are[u][p], ai[u], bim[p]);
           ffma2(aim[u][p], ar[u], bnim[p]);
         }
     }

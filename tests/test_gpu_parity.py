@@ -106,7 +106,7 @@ def test_empty_context_and_empty_batch(env, path):
 @pytest.mark.parametrize("plan", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", [(512, 2, 640, 2), (200, 3, 1000, 2), (130, 2, 300, 2), (64, 3, 4096, 1),
                                    (258, 2, 256, 2), (6, 2, 33, 1), (1, 1, 5, 1), (96, 1, 129, 2), (2048, 1, 256, 2),
-                                   (192, 2, 384, 1)])
+                                   (192, 2, 384, 1), (600, 2, 300, 2), (1000, 1, 256, 1)])
 def test_tile_plans(env, plan, shape):
     """Every work-item plan of the two-pass tensor path is bit-exact: plan 0 (64 x 128 tiles), plan 1 (64 x 64 tiles),
     plan 2 (pairs of 64-input c-blocks sharing one operand tile; a half-width second half on the

@@ -271,7 +271,7 @@ void free_ctx(corr_ctx* c) {
   delete c;
 }
 
-XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush);
+XengArgs xeng_args(const corr_ctx* c, int buf, int T_run, int flush);  // buf: operand buffer d_op (0) or d_op2 (1)
 
 // Accumulate T_blk samples from a device buffer laid out [T_blk][C][N].
 
@@ -302,7 +302,7 @@ int accumulate_device(corr_ctx* c, const uint8_t* d_in, int T_blk, cudaStream_t 
     if (e != cudaSuccess) return cuda_fail(e, "operand build launch");
     tb = timer_begin(c, CORR_KERNEL_XENG, st);
     if (two_pass)
-      e = launch_f8_xeng(xeng_args(c, c->tmap, T_run, flush), c->num_sms, st);
+      e = launch_f8_xeng(xeng_args(c, 0, T_run, flush), c->num_sms, st);
     else
       e = launch_f8_fused(c->L.s, d_in, T_blk, flush, c->d_tiles8, c->n_tiles8, c->d_cross, c->d_autos, c->d_err,
                           c->num_sms, st);
@@ -324,8 +324,12 @@ int set_tile_plan(corr_ctx* c, int plan) {
   const std::vector<F8Tile> tw = plan >= 2 ? f8_tile_plan(c->L.s.N, c->L.R, plan) : t8;
   std::vector<WorkItem> items;
   items.reserve((size_t)c->L.s.C * tw.size());
-  for (int f = 0; f < c->L.s.C; ++f)
-    for (const F8Tile& t : tw) items.push_back(WorkItem{0, f, t.c0, t.a0, t.nb, t.pad});
+  if (c->L.R_buf == 64 && plan < 2) {  // channel pairs (uses_channel_pairs)
+    for (int f = 0; f < c->L.s.C; f += 2) items.push_back(WorkItem{0, f, 0, 0, 128, 0});
+  } else {
+    for (int f = 0; f < c->L.s.C; ++f)
+      for (const F8Tile& t : tw) items.push_back(WorkItem{0, f, t.c0, t.a0, t.nb, t.pad});
+  }
   F8Tile* d_t = nullptr;
   WorkItem* d_i = nullptr;
   if (cudaMalloc(&d_t, t8.size() * sizeof(F8Tile)) != cudaSuccess ||
@@ -359,10 +363,15 @@ int default_tile_plan(int N) {
   return N >= 512 ? 3 : 0;
 }
 
-XengArgs xeng_args(const corr_ctx* c, const CUtensorMap& map, int T_run, int flush) {
+bool uses_channel_pairs(const corr_ctx* c) { return c->L.R_buf == 64 && c->tile_plan < 2; }
+
+XengArgs xeng_args(const corr_ctx* c, int buf, int T_run, int flush) {
   XengArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.a[0].tmap = map;
+  const bool cp = uses_channel_pairs(c);
+  a.a[0].tmap = cp ? (buf ? c->tmap2_cp : c->tmap_cp) : (buf ? c->tmap2 : c->tmap);
+  a.a[0].C = c->L.s.C;
+  a.a[0].cpair = cp ? 1 : 0;
   a.a[0].cross = c->d_cross;
   a.a[0].autos = c->d_autos;
   a.a[0].Bs = c->L.s.Bs;
@@ -389,7 +398,9 @@ int ensure_operand_scratch(corr_ctx* c) {
   cudaError_t e = cudaMemset(c->d_op, 0, c->L.op_buf_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
   std::string err;
-  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
+  if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0 ||
+      (c->L.R_buf == 64 &&
+       encode_op_tensor_map(&c->tmap_cp, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err, true) != 0)) {
     cudaFree(c->d_op);
     c->d_op = nullptr;
     return fail(CORR_ERR_CUDA, err);
@@ -450,7 +461,9 @@ int ensure_overlap(corr_ctx* c) {
     }
     cudaError_t e = cudaMemset(c->d_op2, 0, c->L.op_buf_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "second operand buffer init");
-    if (encode_op_tensor_map(&c->tmap2, c->d_op2, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0) {
+    if (encode_op_tensor_map(&c->tmap2, c->d_op2, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0 ||
+        (c->L.R_buf == 64 && encode_op_tensor_map(&c->tmap2_cp, c->d_op2, c->L.R_buf, c->L.T_pad * c->L.K_batch,
+                                                  c->L.s.C, &err, true) != 0)) {
       cudaFree(c->d_op2);
       c->d_op2 = nullptr;
       return fail(CORR_ERR_CUDA, err);
@@ -506,7 +519,7 @@ int accumulate_batch_overlap(corr_ctx* c, const uint8_t* const* blocks, int n, c
       const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
       // k == S: the build shares every SM with the X-engine (one small build CTA beside each X-engine CTA)
       const int grid_x = (j == J - 1 || k >= S) ? S : S - k;
-      e = launch_f8_xeng(xeng_args(c, buf ? c->tmap2 : c->tmap, nb * T_pad, flush), grid_x, st);
+      e = launch_f8_xeng(xeng_args(c, buf, nb * T_pad, flush), grid_x, st);
       timer_end(c, CORR_KERNEL_XENG, st, tb);
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_op_free[buf], st);
@@ -550,7 +563,7 @@ int accumulate_batch_chunks(corr_ctx* c, const uint8_t* const* blocks, int n, cu
       if (e != cudaSuccess) return cuda_fail(e, "batch operand build");
     }
     const bool tb = timer_begin(c, CORR_KERNEL_XENG, st);
-    const cudaError_t e = launch_f8_xeng(xeng_args(c, c->tmap, nb * T_pad, flush), c->num_sms, st);
+    const cudaError_t e = launch_f8_xeng(xeng_args(c, 0, nb * T_pad, flush), c->num_sms, st);
     timer_end(c, CORR_KERNEL_XENG, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "batch x-engine");
     c->n_off += (long long)T_blk * nb;

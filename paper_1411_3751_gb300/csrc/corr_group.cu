@@ -73,7 +73,12 @@ int group_build_items(corr_group* g) {
   std::vector<WorkItem> items;
   for (int i : order) {
     corr_ctx* c = g->ctx[i];
-    // group launches run the one-SM mode: a member on plan 2 or 3 joins with plan 0
+    // group launches run the one-SM mode: a member on plan 2 or 3 joins with plan 0; members of 64
+    // operand rows (17 .. 32 inputs) as channel pairs
+    if (c->L.R_buf == 64) {
+      for (int f = 0; f < c->L.s.C; f += 2) items.push_back(WorkItem{i, f, 0, 0, 128, 0});
+      continue;
+    }
     const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan >= 2 ? 0 : c->tile_plan);
     for (int f = 0; f < c->L.s.C; ++f)
       for (const F8Tile& t : t8) items.push_back(WorkItem{i, f, t.c0, t.a0, t.nb, 0});
@@ -111,7 +116,9 @@ int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
                                    c->d_soff, c->d_soff_auto, st);
     timer_end(c0, CORR_KERNEL_UNPACK, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "group operand build");
-    a.a[i].tmap = c->tmap;
+    a.a[i].tmap = c->L.R_buf == 64 ? c->tmap_cp : c->tmap;
+    a.a[i].cpair = c->L.R_buf == 64 ? 1 : 0;
+    a.a[i].C = c->L.s.C;
     a.a[i].cross = c->d_cross;
     a.a[i].autos = c->d_autos;
     a.a[i].Bs = c->L.s.Bs;

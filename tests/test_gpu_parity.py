@@ -135,6 +135,66 @@ def test_tile_plans(env, plan, shape):
     assert np.array_equal(c, want_c) and np.array_equal(a, want_a)
 
 
+@pytest.mark.parametrize("shape", [(32, 8, 1024, 2), (32, 7, 300, 2), (17, 5, 129, 1), (24, 1, 256, 2),
+                                   (31, 2, 1000, 1), (18, 3, 4096, 2), (32, 65535, 3, 2)])
+def test_channel_pairs(env, shape):
+    """Arrays of 17 .. 32 inputs (64 operand rows per channel): tile plans 0 and 1 run the two-pass
+    X-engine on channel pairs (channels f and f + 1 stacked in one 128-row tile, the two diagonal
+    blocks of its product drained), plans 2 and 3 one channel per item. Even and odd channel counts
+    (the last pair's second channel past the tensor map's extent), one channel, the largest channel
+    count, ragged T; three blocks in one batch flushed every 128 samples, then a plain block."""
+    corr, synth, torch = env
+    N, C, T, npol = shape
+    host = synth.generate_host(synth.Spec(kind="saturate", seed=N * 11 + C, seg_len=128, m8_segment=1), 4 * T, C, N)
+    want_c, want_a = oracle.correlate(host, npol, threads=8)
+    for plan in (0, 1, 2, 3):
+        with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+            xc.set_tile_plan(plan)
+            xc.set_flush_period(128)
+            xc.accumulate_batch([torch.from_numpy(np.ascontiguousarray(host[b * T:(b + 1) * T])).cuda()
+                                 for b in range(3)])
+            xc.set_flush_period(0)
+            xc.accumulate(torch.from_numpy(np.ascontiguousarray(host[3 * T:])).cuda())
+            c = xc.dump(corr.CORR_WHAT_CROSS).cpu().numpy()
+            a = xc.dump(corr.CORR_WHAT_AUTO).cpu().numpy()
+            xc.sync()
+        bad = np.argwhere(c != want_c)
+        assert bad.size == 0, "plan %d: cross mismatch at %s" % (plan, bad[:3].tolist())
+        assert np.array_equal(a, want_a), "plan %d: autos" % plan
+
+
+def test_channel_pairs_full_size_32_inputs(env):
+    """The small-array workload (32 inputs, 4 blocks of 8192 samples, one batch launch) with an odd
+    channel count, 2401: every cell of sampled channels (both members of the first and last pairs,
+    the unpaired last channel, a middle pair) against the oracle on host-regenerated channels, and the
+    auto-station invariants on every channel."""
+    corr, synth, torch = env
+    N, C, T, B, npol = 32, 2401, 8192, 4, 2
+    spec = synth.Spec(kind="gauss_tone", seed=0x14113751 + 60)
+    blocks = [synth.generate_device(spec, T, C, N, t0=b * T) for b in range(B)]
+    with corr.Correlator(N, C, T, npol, path="fp8tc") as xc:
+        assert xc.tile_plan == 0
+        xc.accumulate_batch(blocks)
+        cross = xc.dump(corr.CORR_WHAT_CROSS, device=False)
+        autos = xc.dump(corr.CORR_WHAT_AUTO, device=False)
+        xc.sync()
+    first = blocks[0][:, 1].cpu().numpy()
+    del blocks
+    cross, autos = cross.numpy(), autos.numpy()
+    for f in (0, 1, 1200, 1201, 2398, 2399, 2400):
+        hf = synth.generate_host(spec, B * T, C, N, c_range=(f, f + 1))
+        if f == 1:
+            assert np.array_equal(hf[:T, 0], first)
+        want_c, want_a = oracle.correlate(hf, npol)
+        assert np.array_equal(cross[f], want_c[0]), "cross mismatch on channel %d" % f
+        assert np.array_equal(autos[f], want_a[0]), "autos mismatch on channel %d" % f
+    S = N // 2
+    diag = np.array([s * (s + 1) // 2 + s for s in range(S)])
+    assert np.array_equal(cross[:, diag, 0, 0], autos[:, 0::2]) and np.array_equal(cross[:, diag, 3, 0], autos[:, 1::2])
+    assert np.array_equal(cross[:, diag, 2, 0], cross[:, diag, 1, 0])
+    assert np.array_equal(cross[:, diag, 2, 1], -cross[:, diag, 1, 1])
+
+
 @pytest.mark.parametrize("N", [512, 200, 6])
 def test_offset_and_signed_paths_in_one_integration(env, N):
     """The FP8 tensor paths multiply offset samples (corrected at the dump with the per-input offset sums

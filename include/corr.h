@@ -454,8 +454,9 @@ int corr_probe_mma_rate(int n_mma, int n_cols, double* tflops, double* cycles_pe
  * corr_group_member   the i-th sub-array's context, for corr_dump / corr_reset / counters; owned by
  *                     the group (do not destroy it).
  * corr_group_accumulate  one block per sub-array (d_samples[i] device uint8[T][C_i][N_i]); mode 0:
- *                     operand builds then ONE grouped X-engine launch; mode 1: separate per-array
- *                     launches (for comparison). Results are identical.
+ *                     ONE operand-build launch over all sub-arrays, then ONE grouped X-engine
+ *                     launch; mode 1: separate per-array launches (for comparison). Results are
+ *                     identical.
  * corr_group_autotune times the two tile plans of each sub-array on the given blocks, keeps the
  *                     faster one (cached in-process by (N, C, T, n_pol, SM count), and in the file
  *                     named by CORR_AUTOTUNE_CACHE if set), then zeroes the accumulators it touched.

@@ -65,7 +65,11 @@ void tune_store(const std::tuple<int, int, int, int, int>& k, int plan) {
   std::fclose(fh);
 }
 
-// Group work list: arrays in order of decreasing N (largest tiles first), each channel-major.
+// Group work list: arrays in order of decreasing N (largest tiles first, the short items of small
+// arrays last, where they even out the tail), each channel-major. (Merging the arrays in proportion
+// to their channel counts, so that HBM-bound small-array items run beside tensor-bound large ones,
+// measured the same: 0.638 against 0.641 ms for 32-512 inputs x 2400-109 channels x 4096 samples,
+// whose X-engine time is the MMA issue of the 200-512-input members.)
 int group_build_items(corr_group* g) {
   std::vector<int> order(g->n);
   for (int i = 0; i < g->n; ++i) order[i] = i;
@@ -99,7 +103,7 @@ int group_build_items(corr_group* g) {
   return CORR_OK;
 }
 
-// One grouped accumulate: operand build per array, then one persistent launch over all arrays.
+// One grouped accumulate: one operand-build launch over all arrays, then one persistent X-engine launch.
 int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
   corr_ctx* c0 = g->ctx[0];
   const int T_pad = c0->L.T_pad;
@@ -109,13 +113,27 @@ int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
     if (!g->ctx[i]->d_op)
       return fail(CORR_ERR_STATE, "group member " + std::to_string(i) +
                                       " has no operand scratch (its path was set to FP32 or int8; set a tensor path)");
+  // every member's operand build in one launch
+  PrepJobDesc jobs[kMaxGroupArrays];
   for (int i = 0; i < g->n; ++i) {
     corr_ctx* c = g->ctx[i];
-    bool tb = timer_begin(c0, CORR_KERNEL_UNPACK, st);
-    cudaError_t e = launch_f8_prep(c->L.s, in[i], c->L.s.T, T_pad, c->L.T_pad * c->L.K_batch, 0, c->L.R_buf, c->d_op,
-                                   c->d_soff, c->d_soff_auto, st);
+    jobs[i].s = c->L.s;
+    jobs[i].in = in[i];
+    jobs[i].T_stride = c->L.T_pad * c->L.K_batch;
+    jobs[i].t_base = 0;
+    jobs[i].R = c->L.R_buf;
+    jobs[i].op = c->d_op;
+    jobs[i].s1 = c->d_soff;
+    jobs[i].s2 = c->d_soff_auto;
+  }
+  {
+    const bool tb = timer_begin(c0, CORR_KERNEL_UNPACK, st);
+    const cudaError_t e = launch_f8_prep_group(jobs, g->n, c0->L.s.T, T_pad, st);
     timer_end(c0, CORR_KERNEL_UNPACK, st, tb);
     if (e != cudaSuccess) return cuda_fail(e, "group operand build");
+  }
+  for (int i = 0; i < g->n; ++i) {
+    corr_ctx* c = g->ctx[i];
     a.a[i].tmap = c->L.R_buf == 64 ? c->tmap_cp : c->tmap;
     a.a[i].cpair = c->L.R_buf == 64 ? 1 : 0;
     a.a[i].C = c->L.s.C;

@@ -126,6 +126,17 @@ cudaError_t launch_f8_fused(const Shape& s, const uint8_t* d_in, int T_blk, int 
 // The block is written at sample offset t_base of each channel's operand rows.
 cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int t_base, int R,
                            uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st);
+// The builds of several arrays (a group of sub-arrays: one block of T_blk samples each, T_run written)
+// in one launch; each job as launch_f8_prep would build it alone.
+struct PrepJobDesc {
+  Shape s;
+  const uint8_t* in;
+  int T_stride, t_base, R;
+  uint8_t* op;
+  long long* s1;
+  long long* s2;
+};
+cudaError_t launch_f8_prep_group(const PrepJobDesc* jobs, int n, int T_blk, int T_run, cudaStream_t st);
 
 // The same operand bytes and offset sums built with TMA loads and stores by at most max_ctas persistent
 // CTAs (one per SM), for running beside the X-engine (prep_tma.cu); f8_prep_tma_supported says whether

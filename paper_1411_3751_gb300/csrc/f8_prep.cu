@@ -2,6 +2,8 @@
 // the GPU): packed bytes in[T][C][N] -> op[C][T_pad][R] (offset e4m3 bytes, group row order, MN-major:
 // one contiguous row of R bytes per channel and sample) plus the per-input offset sums. Streams
 // through HBM. Operand encoding and row order: f8_common.cuh.
+#include <cstring>
+
 #include "corr_internal.cuh"
 #include "f8_common.cuh"
 
@@ -23,18 +25,19 @@ using namespace f8;
 //    int64 sums with one atomic per input and block.
 constexpr int PREP_ROWS_PER_THREAD_MAX = 2048;
 
-__global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int T_run,
-                                                      int T_stride, int t_base, int R, int rows_per_split, bool vec,
-                                                      uint8_t* __restrict__ op, long long* __restrict__ s1,
-                                                      long long* __restrict__ s2) {
+// The build of one block (bx, bz) of the grid: bx picks 8 units, bz the time range.
+__device__ __forceinline__ void prep_block(const uint8_t* __restrict__ in, int N, int C, int T, int T_run, int T_stride,
+                                           int t_base, int R, int rows_per_split, bool vec, uint8_t* __restrict__ op,
+                                           long long* __restrict__ s1, long long* __restrict__ s2, long long bx,
+                                           int bz) {
   const int G = R / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tl = lane >> 3, us = lane & 7;
-  const long long unit = 8LL * blockIdx.x + us;  // flattened unit
+  const long long unit = 8LL * bx + us;  // flattened unit
   const bool unit_ok = unit < (long long)C * G;
   const int f = unit_ok ? (int)(unit / G) : 0;
   const int g = unit_ok ? (int)(unit - (long long)f * G) : G;
-  const int t_begin = blockIdx.z * rows_per_split;
+  const int t_begin = bz * rows_per_split;
   const int t_end = min(T_run, t_begin + rows_per_split);
   const int n0 = 16 * g;
   const int nv = N - n0;  // valid inputs of this unit (<= 0: padding unit)
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   __syncthreads();
   // thread i: unit i / 32, value i % 32
   const int uu = threadIdx.x >> 5, j = threadIdx.x & 31;
-  const long long ug = 8LL * blockIdx.x + uu;
+  const long long ug = 8LL * bx + uu;
   const int fu = (int)(ug / G), gu = (int)(ug - (long long)(ug / G) * G);
   const int n = 16 * gu + (j >> 1);
   if (ug < (long long)C * G && n < N) {
@@ -130,11 +133,40 @@ __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict_
   }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int T_run,
+                                                      int T_stride, int t_base, int R, int rows_per_split, bool vec,
+                                                      uint8_t* __restrict__ op, long long* __restrict__ s1,
+                                                      long long* __restrict__ s2) {
+  prep_block(in, N, C, T, T_run, T_stride, t_base, R, rows_per_split, vec, op, s1, s2, blockIdx.x, blockIdx.z);
+}
 
-cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int t_base, int R,
-                           uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st) {
-  if (T_run == 0) return cudaSuccess;
+// Several arrays' builds in one launch (groups of sub-arrays): job i owns the linear blocks
+// [blk0_i, blk0_{i+1}), gx_i unit blocks by its time split, as its own launch would lay them out.
+struct PrepJob {
+  const uint8_t* in;
+  uint8_t* op;
+  long long* s1;
+  long long* s2;
+  long long blk0;
+  int N, C, R, T_stride, t_base, rows, gx, vec;
+};
+struct PrepGroupArgs {
+  PrepJob job[kMaxGroupArrays];
+  int n, T, T_run;
+};
+
+__global__ void __launch_bounds__(256) f8_prep_group_kernel(const __grid_constant__ PrepGroupArgs a) {
+  const long long b = blockIdx.x;
+  int i = 0;
+  while (i + 1 < a.n && b >= a.job[i + 1].blk0) ++i;
+  const PrepJob& j = a.job[i];
+  const long long local = b - j.blk0;
+  prep_block(j.in, j.N, j.C, a.T, a.T_run, j.T_stride, j.t_base, j.R, j.rows, j.vec != 0, j.op, j.s1, j.s2,
+             local % j.gx, (int)(local / j.gx));
+}
+
+// Grid of one array's build: gx blocks of 8 units by `split` time ranges of `rows` samples.
+void prep_geometry(const Shape& s, int T_run, int R, long long* gx, int* split_out, int* rows_out) {
   const int G = R / 32;
   // time split: at most PREP_ROWS_PER_THREAD_MAX samples per thread (each thread takes one of 32)
   int split = 1;
@@ -146,8 +178,56 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
   const long long target = 8LL * sm_count();
   while ((units + 7) / 8 * split < target && T_run / (split * 2) >= 256) split *= 2;
   const int rows = (int)round_up((T_run + split - 1) / split, 32);
-  split = (T_run + rows - 1) / rows;
-  dim3 grid((unsigned)((units + 7) / 8), 1, split);
+  *split_out = (T_run + rows - 1) / rows;
+  *rows_out = rows;
+  *gx = (units + 7) / 8;
+}
+
+}  // namespace
+
+cudaError_t launch_f8_prep_group(const PrepJobDesc* jobs, int n, int T_blk, int T_run, cudaStream_t st) {
+  if (T_run == 0 || n <= 0) return cudaSuccess;
+  if (n > kMaxGroupArrays) return cudaErrorInvalidValue;
+  PrepGroupArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.T = T_blk;
+  a.T_run = T_run;
+  long long blocks = 0;
+  for (int i = 0; i < n; ++i) {
+    const PrepJobDesc& d = jobs[i];
+    PrepJob& j = a.job[i];
+    int split = 1, rows = 0;
+    long long gx = 0;
+    prep_geometry(d.s, T_run, d.R, &gx, &split, &rows);
+    j.in = d.in;
+    j.op = d.op;
+    j.s1 = d.s1;
+    j.s2 = d.s2;
+    j.blk0 = blocks;
+    j.N = d.s.N;
+    j.C = d.s.C;
+    j.R = d.R;
+    j.T_stride = d.T_stride;
+    j.t_base = d.t_base;
+    j.rows = rows;
+    j.gx = (int)gx;
+    j.vec = (d.s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d.in) % 16) == 0;
+    blocks += gx * split;
+  }
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
+  f8_prep_group_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T_run, int T_stride, int t_base, int R,
+                           uint8_t* d_op, long long* d_s1, long long* d_s2, cudaStream_t st) {
+  if (T_run == 0) return cudaSuccess;
+  int split = 1, rows = 0;
+  long long gx = 0;
+  prep_geometry(s, T_run, R, &gx, &split, &rows);
+  dim3 grid((unsigned)gx, 1, split);
   const bool vec = (s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
   f8_prep_kernel<<<grid, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, t_base, R, rows, vec, d_op, d_s1,
                                        d_s2);

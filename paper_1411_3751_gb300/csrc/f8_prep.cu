@@ -27,7 +27,7 @@ constexpr int PREP_ROWS_PER_THREAD_MAX = 2048;
 
 // The build of one block (bx, bz) of the grid: bx picks 8 units, bz the time range.
 __device__ __forceinline__ void prep_block(const uint8_t* __restrict__ in, int N, int C, int T, int T_run, int T_stride,
-                                           int t_base, int R, int rows_per_split, bool vec, uint8_t* __restrict__ op,
+                                           int t_base, int R, int rows_per_split, int vec, uint8_t* __restrict__ op,
                                            long long* __restrict__ s1, long long* __restrict__ s2, long long bx,
                                            int bz) {
   const int G = R / 32;
@@ -57,8 +57,16 @@ __device__ __forceinline__ void prep_block(const uint8_t* __restrict__ in, int N
         live[u] = t < t_end && t < T && nv > 0;
         if (live[u]) {
           const uint8_t* src = in + ((size_t)t * C + f) * N + n0;
-          if (vec) {
+          if (vec == 16) {
             w[u] = __ldg(reinterpret_cast<const uint4*>(src));
+          } else if (vec == 8) {  // N % 8 == 0: nv is 8 or >= 16
+            const uint2 lo = __ldg(reinterpret_cast<const uint2*>(src));
+            const uint2 hi = nv > 8 ? __ldg(reinterpret_cast<const uint2*>(src) + 1) : make_uint2(0u, 0u);
+            w[u] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+          } else if (vec == 4) {  // N % 4 == 0: nv is a multiple of 4
+            const uint32_t* s4 = reinterpret_cast<const uint32_t*>(src);
+            w[u] = make_uint4(__ldg(s4), nv > 4 ? __ldg(s4 + 1) : 0u, nv > 8 ? __ldg(s4 + 2) : 0u,
+                              nv > 12 ? __ldg(s4 + 3) : 0u);
           } else {
             uint32_t x[4] = {0u, 0u, 0u, 0u};
             for (int k = 0; k < 16; ++k)
@@ -134,7 +142,7 @@ __device__ __forceinline__ void prep_block(const uint8_t* __restrict__ in, int N
 }
 
 __global__ void __launch_bounds__(256) f8_prep_kernel(const uint8_t* __restrict__ in, int N, int C, int T, int T_run,
-                                                      int T_stride, int t_base, int R, int rows_per_split, bool vec,
+                                                      int T_stride, int t_base, int R, int rows_per_split, int vec,
                                                       uint8_t* __restrict__ op, long long* __restrict__ s1,
                                                       long long* __restrict__ s2) {
   prep_block(in, N, C, T, T_run, T_stride, t_base, R, rows_per_split, vec, op, s1, s2, blockIdx.x, blockIdx.z);
@@ -161,8 +169,17 @@ __global__ void __launch_bounds__(256) f8_prep_group_kernel(const __grid_constan
   while (i + 1 < a.n && b >= a.job[i + 1].blk0) ++i;
   const PrepJob& j = a.job[i];
   const long long local = b - j.blk0;
-  prep_block(j.in, j.N, j.C, a.T, a.T_run, j.T_stride, j.t_base, j.R, j.rows, j.vec != 0, j.op, j.s1, j.s2,
+  prep_block(j.in, j.N, j.C, a.T, a.T_run, j.T_stride, j.t_base, j.R, j.rows, j.vec, j.op, j.s1, j.s2,
              local % j.gx, (int)(local / j.gx));
+}
+
+// Widest load (16, 8 or 4 bytes, else 1) that keeps every unit's 16 input bytes aligned: the rows of
+// in[T][C][N] start at multiples of N bytes.
+int load_width(int N, const void* in) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+  for (int w = 16; w >= 4; w /= 2)
+    if (N % w == 0 && a % w == 0) return w;
+  return 1;
 }
 
 // Grid of one array's build: gx blocks of 8 units by `split` time ranges of `rows` samples.
@@ -212,7 +229,7 @@ cudaError_t launch_f8_prep_group(const PrepJobDesc* jobs, int n, int T_blk, int 
     j.t_base = d.t_base;
     j.rows = rows;
     j.gx = (int)gx;
-    j.vec = (d.s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d.in) % 16) == 0;
+    j.vec = load_width(d.s.N, d.in);
     blocks += gx * split;
   }
   if (blocks == 0) return cudaSuccess;
@@ -228,7 +245,7 @@ cudaError_t launch_f8_prep(const Shape& s, const uint8_t* d_in, int T_blk, int T
   long long gx = 0;
   prep_geometry(s, T_run, R, &gx, &split, &rows);
   dim3 grid((unsigned)gx, 1, split);
-  const bool vec = (s.N % 16) == 0 && (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  const int vec = load_width(s.N, d_in);
   f8_prep_kernel<<<grid, 256, 0, st>>>(d_in, s.N, s.C, T_blk, T_run, T_stride, t_base, R, rows, vec, d_op, d_s1,
                                        d_s2);
   return cudaGetLastError();

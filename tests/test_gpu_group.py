@@ -142,6 +142,38 @@ def test_five_uneven_subarrays_graph(env):
     print("five-array group: tile plans %s" % plans)
 
 
+def test_group_channel_pairs_and_build_load_widths(env):
+    """Members of 17-32 inputs (channel pairs, odd and even channel counts) beside larger ones, with
+    input counts whose rows allow 16-, 8-, 4- and 1-byte loads in the one-launch operand build (17, 20,
+    24, 32, 100, 130 inputs), a ragged block length and one polarisation: grouped, separate and graph
+    replay all equal the oracle."""
+    corr, synth, torch = env
+    shapes = [(17, 5), (20, 3), (24, 4), (32, 7), (100, 2), (130, 3)]
+    T, npol = 1000, 1
+    specs = [synth.Spec(kind="saturate", seed=700 + i, seg_len=128, m8_segment=1) for i in range(len(shapes))]
+    blk = [[synth.generate_device(sp, T, c, n, t0=k * T) for sp, (n, c) in zip(specs, shapes)] for k in range(2)]
+    want = [oracle.correlate(np.concatenate([blk[0][i].cpu().numpy(), blk[1][i].cpu().numpy()]), npol, threads=8)
+            for i in range(len(shapes))]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for mode in ("grouped", "separate", "graph"):
+            with corr.Group(shapes, T, npol) as g:
+                if mode == "graph":
+                    bufs = [torch.empty_like(b) for b in blk[0]]
+                    g.capture(bufs, stream)
+                for k in range(2):
+                    if mode == "graph":
+                        for dst, src in zip(bufs, blk[k]):
+                            dst.copy_(src)
+                        g.launch(stream)
+                    else:
+                        g.accumulate(blk[k], separate=(mode == "separate"))
+                for i, m in enumerate(g.members):
+                    c, a = _dump(m, corr)
+                    assert np.array_equal(c, want[i][0]) and np.array_equal(a, want[i][1]), (mode, shapes[i])
+    stream.synchronize()
+
+
 def test_member_path_switch_releases_scratch_and_group_rejects_it(env):
     """Setting a member to the FP32 path releases its operand scratch; the grouped launch then refuses
     with an error (no launch on a missing buffer) and works again once a tensor path is set."""

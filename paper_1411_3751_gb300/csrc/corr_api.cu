@@ -324,8 +324,8 @@ int set_tile_plan(corr_ctx* c, int plan) {
   const std::vector<F8Tile> tw = plan >= 2 ? f8_tile_plan(c->L.s.N, c->L.R, plan) : t8;
   std::vector<WorkItem> items;
   items.reserve((size_t)c->L.s.C * tw.size());
-  if (c->L.R_buf == 64 && plan < 2) {  // channel pairs (uses_channel_pairs)
-    for (int f = 0; f < c->L.s.C; f += 2) items.push_back(WorkItem{0, f, 0, 0, 128, 0});
+  if (channel_group(c->L) > 0 && plan < 2) {  // channel groups (uses_channel_groups)
+    for (int f = 0; f < c->L.s.C; f += channel_group(c->L)) items.push_back(WorkItem{0, f, 0, 0, 128, 0});
   } else {
     for (int f = 0; f < c->L.s.C; ++f)
       for (const F8Tile& t : tw) items.push_back(WorkItem{0, f, t.c0, t.a0, t.nb, t.pad});
@@ -363,15 +363,17 @@ int default_tile_plan(int N) {
   return N >= 512 ? 3 : 0;
 }
 
-bool uses_channel_pairs(const corr_ctx* c) { return c->L.R_buf == 64 && c->tile_plan < 2; }
+int channel_group(const Layout& L) { return L.R_buf == 64 ? 2 : (L.R_buf == 32 ? 4 : 0); }
+
+bool uses_channel_groups(const corr_ctx* c) { return channel_group(c->L) > 0 && c->tile_plan < 2; }
 
 XengArgs xeng_args(const corr_ctx* c, int buf, int T_run, int flush) {
   XengArgs a;
   std::memset(&a, 0, sizeof(a));
-  const bool cp = uses_channel_pairs(c);
+  const bool cp = uses_channel_groups(c);
   a.a[0].tmap = cp ? (buf ? c->tmap2_cp : c->tmap_cp) : (buf ? c->tmap2 : c->tmap);
   a.a[0].C = c->L.s.C;
-  a.a[0].cpair = cp ? 1 : 0;
+  a.a[0].cgroup = cp ? channel_group(c->L) : 0;
   a.a[0].cross = c->d_cross;
   a.a[0].autos = c->d_autos;
   a.a[0].Bs = c->L.s.Bs;
@@ -399,8 +401,8 @@ int ensure_operand_scratch(corr_ctx* c) {
   if (e != cudaSuccess) return cuda_fail(e, "operand scratch init");
   std::string err;
   if (encode_op_tensor_map(&c->tmap, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0 ||
-      (c->L.R_buf == 64 &&
-       encode_op_tensor_map(&c->tmap_cp, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err, true) != 0)) {
+      (channel_group(c->L) > 0 && encode_op_tensor_map(&c->tmap_cp, c->d_op, c->L.R_buf, c->L.T_pad * c->L.K_batch,
+                                                       c->L.s.C, &err, channel_group(c->L)) != 0)) {
     cudaFree(c->d_op);
     c->d_op = nullptr;
     return fail(CORR_ERR_CUDA, err);
@@ -462,8 +464,9 @@ int ensure_overlap(corr_ctx* c) {
     cudaError_t e = cudaMemset(c->d_op2, 0, c->L.op_buf_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "second operand buffer init");
     if (encode_op_tensor_map(&c->tmap2, c->d_op2, c->L.R_buf, c->L.T_pad * c->L.K_batch, c->L.s.C, &err) != 0 ||
-        (c->L.R_buf == 64 && encode_op_tensor_map(&c->tmap2_cp, c->d_op2, c->L.R_buf, c->L.T_pad * c->L.K_batch,
-                                                  c->L.s.C, &err, true) != 0)) {
+        (channel_group(c->L) > 0 && encode_op_tensor_map(&c->tmap2_cp, c->d_op2, c->L.R_buf,
+                                                         c->L.T_pad * c->L.K_batch, c->L.s.C, &err,
+                                                         channel_group(c->L)) != 0)) {
       cudaFree(c->d_op2);
       c->d_op2 = nullptr;
       return fail(CORR_ERR_CUDA, err);

@@ -52,7 +52,7 @@ struct corr_ctx {
   int* d_err;
   uint8_t* d_op;          // operand scratch of the two-pass tensor path (K_batch blocks)
   CUtensorMap tmap;
-  CUtensorMap tmap_cp;    // the same buffer as channel-pair boxes (64 operand rows: 17 .. 32 inputs)
+  CUtensorMap tmap_cp;    // the same buffer as channel-group boxes (64 or 32 operand rows: at most 32 inputs)
   // overlapped batches: the operand of chunk j + 1 is built on prep_sms SMs (TMA build kernel, on
   // prep_stream) while the X-engine multiplies chunk j on the others; d_op2 is the second buffer
   int prep_sms;           // -1: automatic, 0: no overlap
@@ -101,9 +101,12 @@ void timer_end(corr_ctx* c, int k, cudaStream_t st, bool begun);
 int set_tile_plan(corr_ctx* c, int plan);
 // Tile plan a context of N inputs starts with: 3 (SM pairs) from 512 inputs, else 0.
 int default_tile_plan(int N);
-// The two-pass X-engine of this context takes channel-pair items: 64 operand rows per channel
-// (17 .. 32 inputs) and a one-SM tile plan (0 or 1).
-bool uses_channel_pairs(const corr_ctx* c);
+// Channels per item of an array's channel groups: 2 for 64 operand rows per channel (17 .. 32 inputs),
+// 4 for 32 rows (at most 16 inputs), else 0.
+int channel_group(const Layout& L);
+// The two-pass X-engine of this context takes channel-group items: channel_group(L) > 0 and a one-SM
+// tile plan (0 or 1).
+bool uses_channel_groups(const corr_ctx* c);
 // blocks per tensor-core launch of batches (reallocates the operand buffers once the device is idle)
 int set_batch_blocks(corr_ctx* c, int K);
 // largest blocks per launch the operand buffer cap allows for this shape

@@ -77,10 +77,10 @@ int group_build_items(corr_group* g) {
   std::vector<WorkItem> items;
   for (int i : order) {
     corr_ctx* c = g->ctx[i];
-    // group launches run the one-SM mode: a member on plan 2 or 3 joins with plan 0; members of 64
-    // operand rows (17 .. 32 inputs) as channel pairs
-    if (c->L.R_buf == 64) {
-      for (int f = 0; f < c->L.s.C; f += 2) items.push_back(WorkItem{i, f, 0, 0, 128, 0});
+    // group launches run the one-SM mode: a member on plan 2 or 3 joins with plan 0; members of at
+    // most 32 inputs as channel groups
+    if (channel_group(c->L) > 0) {
+      for (int f = 0; f < c->L.s.C; f += channel_group(c->L)) items.push_back(WorkItem{i, f, 0, 0, 128, 0});
       continue;
     }
     const std::vector<F8Tile> t8 = f8_tile_plan(c->L.s.N, c->L.R, c->tile_plan >= 2 ? 0 : c->tile_plan);
@@ -134,8 +134,8 @@ int group_enqueue(corr_group* g, const uint8_t* const* in, cudaStream_t st) {
   }
   for (int i = 0; i < g->n; ++i) {
     corr_ctx* c = g->ctx[i];
-    a.a[i].tmap = c->L.R_buf == 64 ? c->tmap_cp : c->tmap;
-    a.a[i].cpair = c->L.R_buf == 64 ? 1 : 0;
+    a.a[i].tmap = channel_group(c->L) > 0 ? c->tmap_cp : c->tmap;
+    a.a[i].cgroup = channel_group(c->L);
     a.a[i].C = c->L.s.C;
     a.a[i].cross = c->d_cross;
     a.a[i].autos = c->d_autos;

@@ -60,13 +60,14 @@ struct WorkItem {
 // different N correlated in one persistent launch).
 constexpr int kMaxGroupArrays = 8;
 struct XengArray {
-  CUtensorMap tmap;  // operand op[C][T_span][R] (the channel-pair box when cpair is set)
+  CUtensorMap tmap;  // operand op[C][T_span][R] (the channel-group box when cgroup is set)
   long long* cross;
   long long* autos;
   long long Bs;
   int N, npol;
-  int C;      // channels (the channel-pair epilogue skips channel f + 1 == C)
-  int cpair;  // items are channel pairs (f even; c0 = a0 = 0, nb = 128): 64 operand rows per channel
+  int C;       // channels (the channel-group epilogue skips channels past C)
+  int cgroup;  // 0, or channels per item (2: 64 operand rows per channel, 4: 32 rows): items are
+               // channels f .. f + cgroup - 1 stacked in one 128-row tile (c0 = a0 = 0, nb = 128)
 };
 struct XengArgs {
   XengArray a[kMaxGroupArrays];
@@ -195,7 +196,8 @@ cudaError_t launch_dump(const long long* d_acc, long long n_elems, void* d_out, 
 void set_last_error(const std::string& msg);
 
 // Tensor-map encoding through the driver entry point (no libcuda link dependency).
-int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err, bool cpair = false);
+// cgroup 2 or 4: boxes of R = 128 / cgroup rows x 128 samples x cgroup channels (channel groups).
+int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err, int cgroup = 0);
 // Raw input in[T][C][N] as a 3-D map, boxes of 64 inputs x 1 channel x 128 samples, no swizzle.
 int encode_input_tensor_map(CUtensorMap* map, const void* d_in, int N, int C, int T, std::string* err);
 

@@ -33,13 +33,14 @@ constexpr int W_STAGES = 3;
 constexpr int W_STAGE_BYTES = 2 * A_BYTES + 2 * B_ATOM;
 static_assert(W_STAGES * W_STAGE_BYTES <= STAGES * STAGE_BYTES, "wide ring must fit the shared memory of the default");
 
-// Channel pairs (arrays with XengArray::cpair set: 17 .. 32 inputs, 64 operand rows per channel): an
-// item is channels f and f + 1, whose rows one TMA box of 64 rows x 128 samples x 2 channels (64-byte
-// swizzle, the array's tensor map) stacks into a 128-row tile, the two channels being its two 64-row
-// MN atoms (8 KB apart). The M = 128, N = 128 MMA of that tile with itself yields both channels'
-// products as its two diagonal 64 x 64 blocks, which the epilogue drains (the off-diagonal blocks,
-// across channels, are discarded). Without the pairing such an array fills a quarter of each
-// 128 x 128 MMA, with it half. Only the narrow mode (WIDE false) takes such items.
+// Channel groups (arrays with XengArray::cgroup = g set: g = 2 for 17 .. 32 inputs, 64 operand rows per
+// channel; g = 4 for at most 16 inputs, 32 rows): an item is channels f .. f + g - 1, whose rows one TMA
+// box of 128 / g rows x 128 samples x g channels (64- or 32-byte swizzle, the array's tensor map)
+// stacks into a 128-row tile, each channel one MN atom of the tile (16 KB / g apart). The M = 128,
+// N = 128 MMA of that tile with itself yields every channel's products as its g diagonal blocks,
+// which the epilogue drains (the off-diagonal blocks, across channels, are discarded). Without the
+// grouping such an array fills at most a quarter (g = 2) or a sixteenth (g = 4) of each 128 x 128
+// MMA, with it g times that. Only the narrow mode (WIDE false) takes such items.
 template <bool WIDE>
 __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_constant__ XengArgs args) {
   constexpr int RING = WIDE ? W_STAGES : STAGES;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
         const WorkItem tl = items[w];
         const int f = tl.f;
         const CUtensorMap* tmap = &args.a[tl.array].tmap;
-        const bool cp = !WIDE && args.a[tl.array].cpair;  // channel-pair item
+        const bool cp = !WIDE && args.a[tl.array].cgroup > 1;  // channel-group item
         const bool a1 = WIDE && (tl.pad & 0xFFFF) != 0;  // second c-block present
         const uint32_t bytes = cp ? (uint32_t)A_BYTES : A_BYTES * (a1 ? 2 : 1) + (tl.nb == 256 ? B_BYTES : B_ATOM);
         for (int ks = 0; ks < n_k; ++ks) {
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
           uint8_t* a_dst = smem + stage * RING_BYTES;
           uint8_t* b_dst = a_dst + B_OFF;
           ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-          if (cp) {  // channels f, f + 1 (a channel past C reads as zeros)
+          if (cp) {  // channels f .. f + g - 1 (channels past C read as zeros)
             ptx::tma_load_3d(a_dst, tmap, &full[stage], 0, ks * KT, f);
           } else {
             ptx::tma_load_3d(a_dst, tmap, &full[stage], 2 * tl.c0, ks * KT, f);
@@ -139,7 +140,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
       bool ok = true;
       for (long long w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
         const WorkItem tl = items[w];
-        const bool cp = !WIDE && args.a[tl.array].cpair;
+        const int cg = WIDE ? 0 : args.a[tl.array].cgroup;
+        const bool cp = cg > 1;
+        // channel groups: MN-major, swizzle of 128 / cg bytes, 8 samples x 128 / cg rows per atom (SBO),
+        // channel k's rows at k x 16 KB / cg (LBO), 32 samples per MMA
+        const uint32_t cg_rows = cp ? 128u / (uint32_t)cg : 0u;
+        const uint32_t cg_layout = cg == 4 ? 6u : 4u;  // 32- or 64-byte swizzle
         const uint32_t idesc = tl.nb == 256 ? id256 : id128;
         // wide mode, half 1: N = nb1 columns of B starting at atom b1 (0, or 1 on a diagonal pair)
         const int nb1 = WIDE ? (tl.pad & 0xFFFF) : 0;
@@ -163,12 +169,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
             ptx::tc_fence_after();
             const uint32_t a_addr = ptx::smem_u32(smem + stage * RING_BYTES);
             const uint32_t b_addr = a_addr + B_OFF;
-            if (cp) {
-              // MN-major, 64-byte swizzle: 8 samples x 64 rows per 512-byte atom (SBO), the second
-              // channel's 64 rows at +8 KB (LBO); A and B are the same tile, 32 samples = 2 KB per MMA
+            if (cp) {  // A and B are the same tile
 #pragma unroll
               for (int kk = 0; kk < KT / 32; ++kk) {
-                const uint64_t dd = ptx::smem_desc(a_addr + kk * 2048, A_BYTES / 2, 512, 4);
+                const uint64_t dd = ptx::smem_desc(a_addr + kk * 32 * cg_rows, cg_rows * KT, 8 * cg_rows, cg_layout);
                 ptx::mma_f8f6f4(d, dd, dd, id128, (ks > k0 || kk > 0) ? 1u : 0u);
               }
             } else
@@ -229,19 +233,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) f8_xeng_kernel(const __grid_co
           break;
         }
         ptx::tc_fence_after();
-        if (!WIDE && arr.cpair) {
-          // lane quarters 0-1 hold channel f's 64 rows, 2-3 channel f + 1's; each channel's own
-          // columns are chunks 0-1 (f) and 2-3 (f + 1); the tile offsets -32 map the second
-          // channel's rows and columns back to its inputs 0 .. 31
-          const int h = q >> 1;
-          if (it.f + h < arr.C) {
+        if (!WIDE && arr.cgroup > 1) {
+          // channel h = q / (4 / g) of the group holds rows 128 h / g .. and its own columns are the
+          // 32-column chunks (4 / g) h ..; a lane quarter's two warps take one chunk each (g = 4: one
+          // chunk per channel, the second warp idle); the tile offsets -64 h / g map channel h's rows
+          // and columns back to its inputs 0 ..
+          const int qpc = 4 / arr.cgroup;  // lane quarters (and chunks) per channel
+          const int h = q / qpc;
+          if (half < qpc && it.f + h < arr.C) {
             F8Tile th;
-            th.c0 = -32 * h;
-            th.a0 = -32 * h;
+            th.c0 = -(64 / arr.cgroup) * h;
+            th.a0 = th.c0;
             th.nb = 128;
             th.pad = 0;
-            drain_tile(tbase + acc * ACC_COLS, q, lane, 2 * h + half, 4, th, it.f + h, arr.N, arr.npol, arr.Bs, arr.cross,
-                       arr.autos);
+            drain_tile(tbase + acc * ACC_COLS, q, lane, qpc * h + half, 4, th, it.f + h, arr.N, arr.npol, arr.Bs,
+                       arr.cross, arr.autos);
           }
         } else if (!WIDE) {
           drain_tile(tbase + acc * ACC_COLS, q, lane, half, 2, tl, it.f, arr.N, arr.npol, arr.Bs, arr.cross, arr.autos);
@@ -387,21 +393,24 @@ int encode_input_tensor_map(CUtensorMap* map, const void* d_in, int N, int C, in
   return 0;
 }
 
-int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err, bool cpair) {
+int encode_op_tensor_map(CUtensorMap* map, void* d_op, int R, int T_pad, int C, std::string* err, int cgroup) {
   encode_fn_t fn = encode_fn(err);
   if (!fn) return -1;
-  if (cpair && R != 64) {
-    if (err) *err = "channel-pair tensor map needs 64 operand rows";
+  const bool cp = cgroup > 1;
+  if (cp && !((cgroup == 2 && R == 64) || (cgroup == 4 && R == 32))) {
+    if (err) *err = "channel-group tensor map needs 128 / cgroup operand rows (cgroup 2 or 4)";
     return -1;
   }
   const cuuint64_t dims[3] = {(cuuint64_t)R, (cuuint64_t)T_pad, (cuuint64_t)C};
   const cuuint64_t strides[2] = {(cuuint64_t)R, (cuuint64_t)R * (cuuint64_t)T_pad};
-  // one 128-row tile per box: 128 rows of one channel (128-byte swizzle), or 64 rows of each of two
-  // channels (64-byte swizzle, the channel-pair items)
-  const cuuint32_t box[3] = {cpair ? 64u : 128u, (cuuint32_t)KT, cpair ? 2u : 1u};
+  // one 128-row tile per box: 128 rows of one channel (128-byte swizzle), or 128 / g rows of each of g
+  // channels (swizzle of 128 / g bytes, the channel-group items)
+  const cuuint32_t box[3] = {cp ? (cuuint32_t)R : 128u, (cuuint32_t)KT, cp ? (cuuint32_t)cgroup : 1u};
+  const CUtensorMapSwizzle swz =
+      !cp ? CU_TENSOR_MAP_SWIZZLE_128B : (cgroup == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, d_op, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  cpair ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r);

@@ -143,12 +143,12 @@ def test_five_uneven_subarrays_graph(env):
 
 
 def test_group_channel_pairs_and_build_load_widths(env):
-    """Members of 17-32 inputs (channel pairs, odd and even channel counts) beside larger ones, with
-    input counts whose rows allow 16-, 8-, 4- and 1-byte loads in the one-launch operand build (17, 20,
-    24, 32, 100, 130 inputs), a ragged block length and one polarisation: grouped, separate and graph
-    replay all equal the oracle."""
+    """Members of at most 32 inputs (channel groups of 2 or 4, full and partial last groups) beside
+    larger ones, with input counts whose rows allow 16-, 8-, 4- and 1-byte loads in the one-launch
+    operand build (6, 16, 17, 20, 24, 32, 100, 130 inputs), a ragged block length and one
+    polarisation: grouped, separate and graph replay all equal the oracle."""
     corr, synth, torch = env
-    shapes = [(17, 5), (20, 3), (24, 4), (32, 7), (100, 2), (130, 3)]
+    shapes = [(17, 5), (20, 3), (24, 4), (32, 7), (100, 2), (130, 3), (16, 6), (6, 5)]
     T, npol = 1000, 1
     specs = [synth.Spec(kind="saturate", seed=700 + i, seg_len=128, m8_segment=1) for i in range(len(shapes))]
     blk = [[synth.generate_device(sp, T, c, n, t0=k * T) for sp, (n, c) in zip(specs, shapes)] for k in range(2)]

@@ -136,13 +136,16 @@ def test_tile_plans(env, plan, shape):
 
 
 @pytest.mark.parametrize("shape", [(32, 8, 1024, 2), (32, 7, 300, 2), (17, 5, 129, 1), (24, 1, 256, 2),
-                                   (31, 2, 1000, 1), (18, 3, 4096, 2), (32, 65535, 3, 2)])
+                                   (31, 2, 1000, 1), (18, 3, 4096, 2), (32, 65535, 3, 2), (16, 8, 1024, 2),
+                                   (16, 6, 300, 2), (9, 5, 129, 1), (1, 3, 200, 1), (12, 1, 256, 2),
+                                   (16, 65534, 3, 2)])
 def test_channel_pairs(env, shape):
-    """Arrays of 17 .. 32 inputs (64 operand rows per channel): tile plans 0 and 1 run the two-pass
-    X-engine on channel pairs (channels f and f + 1 stacked in one 128-row tile, the two diagonal
-    blocks of its product drained), plans 2 and 3 one channel per item. Even and odd channel counts
-    (the last pair's second channel past the tensor map's extent), one channel, the largest channel
-    count, ragged T; three blocks in one batch flushed every 128 samples, then a plain block."""
+    """Arrays of at most 32 inputs: tile plans 0 and 1 run the two-pass X-engine on channel groups
+    (2 channels of 64 operand rows for 17 .. 32 inputs, 4 channels of 32 rows for at most 16, stacked
+    in one 128-row tile, the diagonal blocks of its product drained), plans 2 and 3 one channel per
+    item. Channel counts that fill the last group and that leave 1 .. 3 of its channels past the
+    tensor map's extent, one channel, the largest channel counts, ragged T; three blocks in one batch
+    flushed every 128 samples, then a plain block."""
     corr, synth, torch = env
     N, C, T, npol = shape
     host = synth.generate_host(synth.Spec(kind="saturate", seed=N * 11 + C, seg_len=128, m8_segment=1), 4 * T, C, N)

@@ -114,9 +114,10 @@ int corr_get_path(const corr_ctx* ctx);
  * 128 a-inputs on a pair of SMs (a cluster of two CTAs sharing 2-SM tensor instructions: each SM
  * fetches a third fewer operand bytes for the same work; the diagonal tiles compute a quarter of
  * their products for nothing). A new context starts on plan 3 from 512 inputs and on plan 0 below.
- * Arrays of 17 to 32 inputs (64 operand rows per channel) run plans 0 and 1 as channel pairs: one
- * item multiplies channels f and f + 1 stacked in one 128-row tile, half the products per operand
- * byte of a one-channel item (group launches do the same for such members).
+ * Arrays of at most 32 inputs run plans 0 and 1 as channel groups: one item multiplies channels
+ * f .. f + g - 1 stacked in one 128-row tile (g = 2 for 17 to 32 inputs, 64 operand rows per channel;
+ * g = 4 for at most 16 inputs, 32 rows), g times the useful products per operand byte of a
+ * one-channel item (group launches do the same for such members).
  * Results are identical for every plan. Waits for the device (queued launches read the current work
  * list). CORR_ERR_ARG for another value. Group launches (corr_group_*) always use plan 0 or 1, and the
  * overlapped build (corr_set_prep_sms) runs with plans 0, 1 and 3. corr_get_tile_plan returns the

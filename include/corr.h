@@ -140,6 +140,15 @@ int corr_get_tile_plan(const corr_ctx* ctx);
 int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles);
 
 /*
+ * corr_channel_group - channels per work item of the two-pass tensor path under `plan` for n_inputs
+ * inputs (host only, no device call): 4 for at most 16 inputs and 2 for 17 to 32 inputs under plans
+ * 0 and 1 (the channel groups of corr_set_tile_plan: one item multiplies channels f .. f + g - 1,
+ * f a multiple of g, with c0 = a0 = 0 and nb = 128), else 1 (an item per channel and tile of
+ * corr_tile_plan). CORR_ERR_ARG for n_inputs outside 1 .. 2^20 or plan outside 0 .. 3.
+ */
+int corr_channel_group(int n_inputs, int plan);
+
+/*
  * corr_set_prep_sms - how corr_accumulate_batch schedules the two passes of the tensor path (Sec. 2.4's
  * unpack ahead of Sec. 2.5's cross-multiply). With 0 < sms < SMs, a batch of more than one launch
  * builds the operand of launch j + 1 on `sms` SMs of its own (a TMA-fed build kernel on an internal

@@ -32,6 +32,7 @@ SIGNATURES = [
     ("corr_set_tile_plan", _c_int, [_c_vp, _c_int]),
     ("corr_get_tile_plan", _c_int, [_c_vp]),
     ("corr_tile_plan", _c_int, [_c_int, _c_int, _c_vp, _c_int]),
+    ("corr_channel_group", _c_int, [_c_int, _c_int]),
     ("corr_set_prep_sms", _c_int, [_c_vp, _c_int]),
     ("corr_get_prep_sms", _c_int, [_c_vp]),
     ("corr_set_batch_blocks", _c_int, [_c_vp, _c_int]),
@@ -137,6 +138,11 @@ def corr_tile_plan(n_inputs: int, plan: int):
     buf = (ctypes.c_int * (4 * max(n, 1)))()
     _check(_lib.corr_tile_plan(n_inputs, plan, buf, n), "corr_tile_plan")
     return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
+
+
+def corr_channel_group(n_inputs: int, plan: int) -> int:
+    """Channels per work item of the two-pass tensor path (host only): 4, 2 or 1."""
+    return _check(_lib.corr_channel_group(n_inputs, plan), "corr_channel_group")
 
 
 def corr_set_prep_sms(ctx: int, sms: int) -> int:

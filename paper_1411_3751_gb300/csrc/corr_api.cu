@@ -898,6 +898,15 @@ int corr_tile_plan(int n_inputs, int plan, int* tiles_out, int max_tiles) {
   return (int)t.size();
 }
 
+int corr_channel_group(int n_inputs, int plan) {
+  if (n_inputs < 1 || n_inputs > (1 << 20) || plan < 0 || plan > 3)
+    return fail(CORR_ERR_ARG, "corr_channel_group: need 1 <= n_inputs <= 2^20, plan 0..3");
+  Layout L{};
+  L.R_buf = (int)round_up(2LL * n_inputs, 32);
+  const int g = plan < 2 ? channel_group(L) : 0;
+  return g > 1 ? g : 1;
+}
+
 int corr_selftest_wait(corr_ctx* c, int limit_ms, void* stream) {
   if (!c) return fail(CORR_ERR_ARG, "corr_selftest_wait: NULL context");
   if (limit_ms < 1 || limit_ms > 2000) return fail(CORR_ERR_ARG, "corr_selftest_wait: limit_ms must be in [1, 2000]");

@@ -146,6 +146,28 @@ def test_tile_plans_cover_the_triangle_exactly_once(plan):
         corr.corr_tile_plan(8, 4)
 
 
+def test_channel_group_rule():
+    """Host logic of the channel groups: under tile plans 0 and 1 an array of at most 16 inputs
+    (32 operand rows per channel) multiplies 4 channels per work item and one of 17 .. 32 inputs (64
+    rows) 2, each item being the one tile (0, 0, 128) of the plan that covers the whole triangle, so
+    that the g channels fill the tile's 128 rows exactly; every other case takes one channel per
+    item."""
+    from paper_1411_3751_gb300 import corr
+
+    for N in list(range(1, 70)) + [96, 512, 1 << 20]:
+        for plan in range(4):
+            g = corr.corr_channel_group(N, plan)
+            want = (4 if N <= 16 else 2 if N <= 32 else 1) if plan < 2 else 1
+            assert g == want, (N, plan, g)
+            if g > 1:
+                rows = -(-2 * N // 32) * 32  # operand rows stored per channel
+                assert g * rows == 128, (N, g)
+                assert corr.corr_tile_plan(N, plan) == [(0, 0, 128, 0)], (N, plan)
+    for bad in ((0, 0), (1 << 21, 0), (8, 4), (8, -1)):
+        with pytest.raises(corr.CorrError):
+            corr.corr_channel_group(*bad)
+
+
 def test_batch_launch_length_rule():
     """Host logic of corr_accumulate_batch's launch length: the benchmark's 512-input shape shares
     4 blocks of 8192 samples per launch, 256 inputs 2; every launch stays within 65536 samples (the

@@ -9,7 +9,8 @@
 //                  a-side rows, K = 32 samples per instruction), 2 TMEM accumulators of 256 columns
 //      warps 2-9   epilogue: drain of one accumulator while the MMAs fill the other
 //    Work item = (channel, triangle tile); tiles cover only station pairs a >= c (triangle-only
-//    scheduling), with half-width tiles on the diagonal to cut wasted products.
+//    scheduling), with half-width tiles on the diagonal to cut wasted products; arrays of at most 32
+//    inputs take items of 2 or 4 channels stacked in one tile (channel groups, below).
 #include <cstdio>
 
 #include "corr_internal.cuh"
